@@ -1,0 +1,155 @@
+/*
+ * gn.h — C ABI of the GB300 Gauss-Newton library for sparse polynomial systems
+ * in complex double, double double and quad double arithmetic.
+ *
+ * The operations follow J. Verschelde and X. Yu, "GPU acceleration of Newton's
+ * method for large systems of polynomial equations in double double and quad
+ * double arithmetic" (2014):
+ *   - systems are given in sparse distributed form (Section 1, Problem
+ *     Statement): fully expanded, only monomials with a nonzero coefficient;
+ *   - evaluation and differentiation use common factors (Section 2.1, eq. 1),
+ *     the Speelpenning product and gradient (Section 2.2) and term sums
+ *     (Section 2.3);
+ *   - the least-squares update comes from modified Gram-Schmidt on [A b]
+ *     (Section 3, eq. 2) and back substitution (eq. 5);
+ *   - a Newton step is A = J_f(x0), b = -f(x0), A dx = b, x1 = x0 + dx
+ *     (Section 4), taken in the least-squares sense (Gauss-Newton).
+ *
+ * Conventions shared by every call:
+ *   - A complex number at precision L (L = 1, 2, 4) is 2L doubles: the L limbs
+ *     of the real part, then the L limbs of the imaginary part.  Each part is
+ *     a cascade of doubles (limb l+1 holds what limbs 0..l leave over).  For
+ *     L = 1 this is the layout of C99 double complex.
+ *   - Pointers named d_* are device pointers the caller owns; pointers named
+ *     h_* are host pointers the caller owns.  The library never frees them.
+ *   - Every call is stream-ordered on the given CUDA stream (NULL = legacy
+ *     default stream) and returns a status; errors never cross the ABI in any
+ *     other form.  Device-side failures (a singular pivot, a NaN) are recorded
+ *     in a status word that the call reads back after its kernels, so calls
+ *     that report such conditions synchronize the stream.
+ *   - One gn_system may be used from one host thread and one stream at a time.
+ *   - Link with -lgn (libgn.so); the library needs only the CUDA runtime.
+ */
+#ifndef GN_H
+#define GN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Working precision; the value is the number of limbs L. */
+typedef enum { GN_D = 1, GN_DD = 2, GN_QD = 4 } gn_prec;
+
+typedef enum {
+  GN_OK = 0,
+  GN_EINVAL = 1,     /* invalid argument or malformed system */
+  GN_ENOMEM = 2,     /* device or host allocation failed */
+  GN_ECUDA = 3,      /* a CUDA runtime call failed */
+  GN_ESINGULAR = 4,  /* rank-deficient Jacobian: r_kk <= 2^(8-50L) ||a_k|| */
+  GN_ENOCONV = 5,    /* tolerance not reached within the allowed steps */
+  GN_ENONFINITE = 6, /* NaN or Inf in f, J or the update */
+  GN_ETIMEOUT = 7    /* a bounded device-side wait gave up */
+} gn_status;
+
+/* Opaque, library-owned handle holding a system in device memory. */
+typedef struct gn_system gn_system;
+
+#define GN_REPORT_MAX 64
+
+/* Per-step record of gn_newton, host-owned. */
+typedef struct {
+  int32_t steps_done;               /* steps whose update was applied */
+  int32_t status;                   /* gn_status of the run */
+  double res_norm[GN_REPORT_MAX];   /* ||f(x_k)||_2 before step k (leading limbs) */
+  double dx_norm[GN_REPORT_MAX];    /* ||dx_k||_2 of step k (leading limbs) */
+} gn_report;
+
+/*
+ * Load a system in sparse distributed form (Section 1).  All arrays are host
+ * arrays read once; the caller keeps ownership.
+ *   N, n        : number of polynomials and of variables, N >= n >= 1.
+ *   T           : total number of monomials (terms) over all polynomials.
+ *   h_poly_ptr  : [N+1], monomials of polynomial i are [h_poly_ptr[i], h_poly_ptr[i+1]).
+ *   h_mono_ptr  : [T+1], the support of monomial t is h_var[h_mono_ptr[t] ..
+ *                 h_mono_ptr[t+1]) with exponents h_exp[...]; an empty support
+ *                 is a constant term.
+ *   h_var       : variable indices in [0, n); no variable twice in one monomial.
+ *   h_exp       : exponents d >= 1 (eq. 1: the monomial is x_{i1}^{d1} ... x_{ik}^{dk}).
+ *   h_coef      : [T][2][coef_limbs] doubles: re limbs then im limbs per term.
+ *   coef_limbs  : 1, 2 or 4; a run at precision L uses the first min(L, coef_limbs)
+ *                 limbs of each part (higher ones taken as 0).
+ * Limits: n < 2^24, exponents <= 255, total support length < 2^31.
+ * Returns GN_EINVAL for N < n, a variable out of range or repeated within a
+ * monomial, an exponent of 0, non-monotone pointers, or null pointers.
+ * On success *out owns device memory until gn_system_destroy.
+ */
+gn_status gn_system_create(gn_system **out, int32_t N, int32_t n, int64_t T,
+                           const int64_t *h_poly_ptr, const int64_t *h_mono_ptr,
+                           const int32_t *h_var, const uint8_t *h_exp,
+                           const double *h_coef, int32_t coef_limbs);
+
+/* Free a system and all workspaces it holds (synchronizes the device). */
+gn_status gn_system_destroy(gn_system *s);
+
+/* Basic facts about a loaded system (any pointer may be NULL). */
+gn_status gn_system_info(const gn_system *s, int32_t *N, int32_t *n, int64_t *T,
+                         int64_t *nnz, int32_t *max_support);
+
+/*
+ * Evaluate and differentiate (Section 2): f(x) and the Jacobian J(x).
+ *   d_x : [n] complex at precision prec (2*prec doubles each).
+ *   d_f : [N] complex, output; may be NULL to skip f.
+ *   d_J : N x n complex, column-major (entry (i, v) at index v*ldJ + i),
+ *         output; entries no term touches are set to 0.  May be NULL.
+ *   ldJ : leading dimension of d_J in entries, >= N.
+ * Stream-ordered; does not synchronize.  Uses workspace owned by s.
+ */
+gn_status gn_eval(gn_system *s, gn_prec prec, const double *d_x, double *d_f,
+                  double *d_J, int64_t ldJ, void *cuda_stream);
+
+/*
+ * Least squares by modified Gram-Schmidt on the augmented matrix [A b]
+ * (Section 3, figure "The modified Gram-Schmidt orthogonalization algorithm",
+ * eq. 2), then back substitution R dx = y (eq. 5).
+ *   d_Ab : m x (n+1) complex, column-major with leading dimension ldAb >= m;
+ *          columns 0..n-1 are A, column n is b.  Overwritten: columns 0..n-1
+ *          by Q, column n by b - Q y (its norm is z of eq. 2).
+ *   d_R  : (n+1) x (n+1) complex, column-major, ld n+1, output (may be NULL to
+ *          use library workspace); R[k][k] real positive, R[0:n, n] = y,
+ *          R[n][n] = z, zeros below the diagonal.
+ *   d_dx : [n] complex, output: the least-squares solution of A dx = b.
+ * Returns GN_ESINGULAR (after synchronizing) when a pivot r_kk, k < n, is at
+ * most 2^(8-50L) times the original norm of column k.
+ */
+gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
+                   int64_t ldAb, double *d_R, double *d_dx, void *cuda_stream);
+
+/*
+ * Take up to `steps` Gauss-Newton steps (Section 4) in place on d_x:
+ * evaluate f and J (Section 2), solve [J, -f] by MGS least squares (Section 3),
+ * x <- x + dx.  The whole loop stays on the device; the host reads back only
+ * the per-step norms once at the end (or once per step when tol > 0, to test
+ * ||dx|| <= tol * ||x||).
+ *   d_x    : [n] complex at precision prec, updated in place.
+ *   steps  : 1 .. GN_REPORT_MAX.
+ *   tol    : 0 to always take `steps` steps; > 0 to stop early, GN_ENOCONV if
+ *            never reached.
+ *   report : host-owned, may be NULL.
+ * Synchronizes the stream before returning.
+ */
+gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, double tol,
+                    gn_report *report, void *cuda_stream);
+
+/* Human-readable name of a status. */
+const char *gn_status_str(gn_status st);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t gn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GN_H */

@@ -1,0 +1,65 @@
+// internal.h — library-internal declarations shared by the .cu files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gn.h"
+
+namespace gn {
+
+// One workspace per precision, allocated on first use.
+struct Workspace {
+  bool ready = false;
+  double *pow = nullptr;        // [pmax][n] complex: plane p holds x^(p+1)
+  double *stage_val = nullptr;  // [T] complex: value of each term
+  double *stage_d = nullptr;    // [nnz] complex: d_s * partial of each occurrence
+  double *Ab = nullptr;         // N x (n+1) complex, column-major, ld N
+  double *R = nullptr;          // (n+1) x (n+1) complex, column-major
+  double *dx = nullptr;         // [n] complex
+  double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, then [n+1] original column norms
+  double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
+  int32_t *status = nullptr;    // sticky device status word
+  double *h_norms = nullptr;    // pinned host copy of norms
+  int32_t *h_status = nullptr;  // pinned host copy of status
+  // CUDA graph of one Newton step for a given x pointer and stream
+  cudaGraphExec_t step_exec = nullptr;
+  const double *graph_x = nullptr;
+  cudaStream_t graph_stream = nullptr;
+};
+
+}  // namespace gn
+
+struct gn_system {
+  int32_t N = 0, n = 0;
+  int64_t T = 0, nnz = 0;
+  int32_t kmax = 0, dmax = 1, pmax = 1;
+  int32_t *d_poly_ptr = nullptr;  // [N+1] term ranges
+  int32_t *d_mono_off = nullptr;  // [T+1] occurrence offsets
+  uint32_t *d_occ = nullptr;      // [nnz] (var << 8) | exp
+  double *d_coef = nullptr;       // [4 limbs][2 parts][T] limb-planar coefficients
+  // Jacobian pattern in column-major order (by column, then row)
+  int64_t nz = 0;
+  int32_t *d_jz_row = nullptr;  // [nz]
+  int32_t *d_jz_col = nullptr;  // [nz]
+  int32_t *d_jz_ptr = nullptr;  // [nz+1] into d_jz_occ
+  int32_t *d_jz_occ = nullptr;  // [nnz] occurrence indices, term order within an entry
+  gn::Workspace ws[5];
+};
+
+namespace gn {
+
+gn_status workspace_get(gn_system *s, int L, Workspace **out);
+
+// eval.cu
+gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
+                      double *d_J, int64_t ldJ, cudaStream_t st);
+
+// lstsq.cu
+gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
+                       double *d_R, double *rinv, double *d_dx, int32_t *d_status,
+                       cudaStream_t st);
+gn_status launch_update(int L, int32_t n, double *d_x, const double *d_dx, const double *d_fnorm,
+                        double *d_norms, int32_t *d_status, cudaStream_t st);
+
+}  // namespace gn

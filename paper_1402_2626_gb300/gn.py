@@ -1,0 +1,170 @@
+"""Python binding of the C ABI in include/gn.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA kernels of ``libgn.so``; this
+module only turns torch tensors into device pointers and streams.  It never
+falls back to a CPU path: if the library is missing or no CUDA device is
+present, calls raise.
+
+Tensor layouts (float64, contiguous, on the CUDA device):
+  x, dx : [n, 2, L]        complex vector, re limbs then im limbs
+  f     : [N, 2, L]
+  J     : [n, N, 2, L]     column-major Jacobian: J[v, i] is d f_i / d x_v
+  Ab    : [n+1, m, 2, L]   column-major augmented matrix [A b]
+  R     : [n+1, n+1, 2, L] column-major: R[j, k] is r_kj
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import inputs
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgn.so")
+
+PREC = {"d": 1, "dd": 2, "qd": 4, 1: 1, 2: 2, 4: 4}
+STATUS = {0: "GN_OK", 1: "GN_EINVAL", 2: "GN_ENOMEM", 3: "GN_ECUDA", 4: "GN_ESINGULAR",
+          5: "GN_ENOCONV", 6: "GN_ENONFINITE", 7: "GN_ETIMEOUT"}
+REPORT_MAX = 64
+
+# exported symbols declared in include/gn.h
+SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_info", "gn_eval", "gn_lstsq",
+           "gn_newton", "gn_status_str", "gn_version")
+
+
+class GnError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        name = STATUS.get(status, str(status))
+        super().__init__(f"{what}: {name}")
+        self.status = status
+
+
+class Report(C.Structure):
+    _fields_ = [("steps_done", C.c_int32), ("status", C.c_int32),
+                ("res_norm", C.c_double * REPORT_MAX), ("dx_norm", C.c_double * REPORT_MAX)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libgn.so (built by ``paper_1402_2626_gb300.build``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_1402_2626_gb300.build.build()")
+        L = C.CDLL(path)
+        vp, dp, i64p = C.c_void_p, C.c_double, C.POINTER(C.c_int64)
+        L.gn_system_create.argtypes = [C.POINTER(vp), C.c_int32, C.c_int32, C.c_int64, i64p, i64p,
+                                       C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
+                                       C.POINTER(C.c_double), C.c_int32]
+        L.gn_system_create.restype = C.c_int
+        L.gn_system_destroy.argtypes = [vp]
+        L.gn_system_destroy.restype = C.c_int
+        L.gn_system_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i64p, i64p,
+                                     C.POINTER(C.c_int32)]
+        L.gn_system_info.restype = C.c_int
+        L.gn_eval.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, vp]
+        L.gn_eval.restype = C.c_int
+        L.gn_lstsq.argtypes = [vp, C.c_int, C.c_int32, C.c_int32, vp, C.c_int64, vp, vp, vp]
+        L.gn_lstsq.restype = C.c_int
+        L.gn_newton.argtypes = [vp, C.c_int, vp, C.c_int32, dp, C.POINTER(Report), vp]
+        L.gn_newton.restype = C.c_int
+        L.gn_status_str.argtypes = [C.c_int]
+        L.gn_status_str.restype = C.c_char_p
+        L.gn_version.restype = C.c_int32
+        _lib = L
+        return L
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or t.dtype.is_complex or str(t.dtype) != "torch.float64" or not t.is_contiguous():
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise GnError(st, what)
+
+
+class System:
+    """A polynomial system loaded into device memory (owns a gn_system)."""
+
+    def __init__(self, system: inputs.System, coef_limbs: int = 4):
+        L = load_library()
+        self.N, self.n, self.T = system.N, system.n, system.T
+        self._keep = [np.ascontiguousarray(system.poly_ptr, np.int64),
+                      np.ascontiguousarray(system.mono_ptr, np.int64),
+                      np.ascontiguousarray(system.var, np.int32),
+                      np.ascontiguousarray(system.exp, np.uint8),
+                      np.ascontiguousarray(system.coef[:, :, :coef_limbs], np.float64)]
+        pp, mp, var, ex, cf = self._keep
+        h = C.c_void_p()
+        st = L.gn_system_create(C.byref(h), system.N, system.n, system.T,
+                                pp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                mp.ctypes.data_as(C.POINTER(C.c_int64)),
+                                var.ctypes.data_as(C.POINTER(C.c_int32)),
+                                ex.ctypes.data_as(C.POINTER(C.c_uint8)),
+                                cf.ctypes.data_as(C.POINTER(C.c_double)), coef_limbs)
+        _check(st, "gn_system_create")
+        self._h = h
+        self._lib = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gn_system_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        N, n, mx = C.c_int32(), C.c_int32(), C.c_int32()
+        T, nnz = C.c_int64(), C.c_int64()
+        _check(self._lib.gn_system_info(self._h, C.byref(N), C.byref(n), C.byref(T), C.byref(nnz),
+                                        C.byref(mx)), "gn_system_info")
+        return dict(N=N.value, n=n.value, T=T.value, nnz=nnz.value, max_support=mx.value)
+
+    def eval(self, prec, x, f=None, J=None, stream=None):
+        """f(x) into f [N,2,L] and J into J [n,N,2,L] (column-major), in place."""
+        ldJ = self.N if J is None else J.shape[1]
+        _check(self._lib.gn_eval(self._h, PREC[prec], _ptr(x), _ptr(f), _ptr(J), ldJ,
+                                 _stream(stream)), "gn_eval")
+
+    def lstsq(self, prec, Ab, R, dx, stream=None):
+        """MGS least squares on Ab [n+1, m, 2, L] in place; R and dx are outputs."""
+        ncols, m = Ab.shape[0], Ab.shape[1]
+        _check(self._lib.gn_lstsq(self._h, PREC[prec], m, ncols - 1, _ptr(Ab), m, _ptr(R), _ptr(dx),
+                                  _stream(stream)), "gn_lstsq")
+
+    def newton(self, prec, x, steps, tol=0.0, stream=None, raise_on_error=True):
+        """``steps`` Gauss-Newton steps in place on x [n,2,L]; returns the report."""
+        rep = Report()
+        st = self._lib.gn_newton(self._h, PREC[prec], _ptr(x), steps, float(tol), C.byref(rep),
+                                 _stream(stream))
+        out = dict(status=st, steps_done=rep.steps_done,
+                   res_norm=list(rep.res_norm[: rep.steps_done]),
+                   dx_norm=list(rep.dx_norm[: rep.steps_done]))
+        if raise_on_error and st != 0:
+            raise GnError(st, "gn_newton")
+        return out

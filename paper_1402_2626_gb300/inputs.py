@@ -40,6 +40,7 @@ perturbation.
 
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass, field
 from fractions import Fraction
@@ -272,7 +273,9 @@ WORKLOADS = {
 }
 
 
+@functools.lru_cache(maxsize=8)
 def workload(name: str, system_index: int = 0) -> System:
+    """Named workload (cached: callers must not modify the returned arrays)."""
     w = WORKLOADS[name]
     seed = BASE_SEED + 1000 * w["config"] + system_index
     return random_system(w["N"], w["n"], w["M"], w["k"], w["dmax"], seed, name=name)
