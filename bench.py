@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of the Gauss-Newton hot path on GB300.
+
+Workload: the plain Gauss-Newton system at scale (n = N = 256 variables and
+equations, 256 terms of 16 distinct variables per polynomial, exponents
+uniform in 1..5, unit-modulus coefficients, exact root built in), complex
+double double.  A step is one whole Gauss-Newton step from the perturbed
+start point x* + 1e-6: evaluate f and J (Section 2), MGS least squares on
+[J, -f] (Section 3), x += dx (Section 4), through the C ABI call gn_newton.
+
+The JSON line reports Newton steps/s as ``value`` (device-timed, inputs
+resident), the same through host buffers as ``e2e``, per-precision
+evaluation/differentiation throughput (monomials/s) and least-squares
+times, the roofline of the dominant kernel group, and the CPU oracle timed
+on this machine's host cores.
+
+Under torchrun each rank solves its own independent system (weak scaling,
+no collective on the data path).  ``--impl reference`` times the CPU oracle
+on the same workload and metric.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "complex DD/QD monomial eval+diff/s; Newton steps/s; % of FP64 peak vs plain"
+UNIT = "Newton steps/s"
+WORKLOAD = "gn256"
+L2_BYTES = 129 * 2 ** 20
+# FP64 issue rate used as the ALU roofline: 2 FP64 lanes per clock per SM
+# (the nominal 1.25 TFLOP/s FMA rate of GB300) x 152 SMs x 2070 MHz.
+FP64_PEAK_GINSTR = 2 * 152 * 2.070
+PRECS = {"d": 1, "dd": 2, "qd": 4}
+
+# FP64 instructions (DADD, DMUL, DFMA each one) per complex operation of the
+# device arithmetic in csrc/mw.cuh, counted from the source.
+FP64_COST = {
+    1: dict(mul=4, add=2, scale=2, mul_real=2, abs2=2),
+    2: dict(mul=38, add=22, scale=12, mul_real=14, abs2=19),
+    4: dict(mul=456, add=152, scale=128, mul_real=232, abs2=228),
+}
+
+
+def algorithmic_fp64(system, L):
+    """FP64 instructions of one evaluation (Section 2) and one MGS least-squares
+    solve (Section 3) of ``system``, from the operation counts of the method
+    and the per-operation costs above."""
+    import numpy as np
+
+    c = FP64_COST[L]
+    k = np.diff(system.mono_ptr)
+    ell = np.add.reduceat((system.exp >= 2).astype(np.int64), system.mono_ptr[:-1]) \
+        if system.nnz else np.zeros_like(k)
+    ell = np.where(k > 0, ell, 0)
+    mults = np.where(k >= 2, 3 * k - 3, np.where(k == 1, 1, 0)) + ell
+    pmax = max(int(system.exp.max()) - 1, 1)
+    eval_ops = int(mults.sum()) * c["mul"] + int(k.sum()) * c["scale"]
+    eval_ops += system.n * (pmax - 1) * c["mul"]
+    # term sums: about one complex addition per contribution (J) and per term (f)
+    eval_ops += (system.nnz + system.T) * c["add"]
+    m, n = system.N, system.n
+    pairs = m * n * (n + 1) // 2
+    mgs_ops = pairs * 2 * (c["mul"] + c["add"]) + (n + 1) * m * (c["abs2"] + c["add"] + c["mul_real"])
+    back_ops = n * (n - 1) // 2 * (c["mul"] + c["add"]) + n * c["mul_real"]
+    return eval_ops, mgs_ops + back_ops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                p = [q.strip() for q in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    mx.append(float(p[2]))
+                except ValueError:
+                    continue
+                for nm, flag in zip(names, p[5:9]):
+                    if flag.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def oracle_steps(system, L, nsteps, nthreads):
+    """Time ``nsteps`` Gauss-Newton steps of the CPU oracle (from x0 each)."""
+    import oracle
+
+    x0 = system.point("x0", L)
+    times = []
+    for _ in range(nsteps):
+        t = time.perf_counter()
+        oracle.newton_step(system, x0, L, nthreads=nthreads)
+        times.append(time.perf_counter() - t)
+    return times
+
+
+def cpu_baseline(system, L, budget_s=15.0):
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    times = []
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and len(times) < 20:
+        times.extend(oracle_steps(system, L, 1, cores))
+    return {"value": len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} full Gauss-Newton steps of the {WORKLOAD} workload in "
+                      f"{ {1: 'D', 2: 'DD', 4: 'QD'}[L]} ({sum(times):.1f} s)"}
+
+
+def run_reference(args):
+    """The CPU oracle on the same workload, metric and steps (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1402_2626_gb300 import inputs
+
+    import oracle
+
+    oracle.build()
+    L = PRECS[args.prec]
+    system = inputs.workload(WORKLOAD, 0)
+    cores = os.cpu_count() or 1
+    oracle_steps(system, L, args.warmup, cores)
+    times = oracle_steps(system, L, args.steps, cores)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": 256, "n": 256, "terms_per_poly": 256, "k": 16,
+                   "dmax": 5, "precision": args.prec},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full Gauss-Newton steps, CPU oracle, {cores} threads"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="dd", choices=list(PRECS))
+    ap.add_argument("--no-extras", action="store_true", help="skip per-precision breakdowns")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_1402_2626_gb300 import build, gn, inputs
+
+    if local == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    L = PRECS[args.prec]
+    system = inputs.workload(WORKLOAD, rank)
+    S = gn.System(system)
+    x0 = torch.tensor(system.point("x0", L), device=dev)
+    x = x0.clone()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.newton(args.prec, x, 1)
+
+    for _ in range(max(args.warmup, 3)):
+        x.copy_(x0)
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps (outside the events)
+    clocks = ClockSampler(torch.cuda.current_device())
+    if rank == 0:
+        clocks.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        x.copy_(x0)
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if rank == 0 else {}
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    t_local = sum(step_ms) / 1e3
+    t_max = t_local
+    if dist:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps / t_max
+    launches_per_step = 4 + 1 + (system.n + 1) + system.n + 2
+
+    # ---- end to end through host buffers: H2D of x, gn_newton, D2H of x
+    hx0 = torch.tensor(system.point("x0", L)).pin_memory()
+    hx = torch.empty_like(hx0).pin_memory()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        x.copy_(hx0, non_blocking=True)
+        step()
+        hx.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t))
+    e2e_local = sum(e2e_ms) / 1e3
+    if dist:
+        tt = torch.tensor([e2e_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_local = float(tt.item())
+    e2e = {"value": world * args.steps / e2e_local, "unit": UNIT,
+           "h2d_bytes_per_step": int(hx0.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8 + 8 * 2 * 64 * 3)}
+
+    extras = {}
+    roofline = None
+    if rank == 0 and not args.no_extras:
+        extras, roofline = breakdown(S, system, dev, flush, args)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": system.N, "n": system.n, "terms_per_poly": 256,
+                       "k": 16, "dmax": 5, "T": system.T, "precision": args.prec,
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk, "roofline": roofline, **extras,
+        }
+        if not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline(system, L)
+        print(json.dumps(line), flush=True)
+    S.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def breakdown(S, system, dev, flush, args):
+    """Per-precision eval+diff and least-squares times (device events, L2 flushed)."""
+    import torch
+
+    from paper_1402_2626_gb300 import gn
+
+    reps = max(5, min(args.steps, 20))
+    stream = torch.cuda.current_stream(dev)
+    out = {"eval_diff": {}, "lstsq_ms": {}, "newton_step_ms": {}}
+    roof = None
+    for prec, L in PRECS.items():
+        x = torch.tensor(system.point("x0", L), device=dev)
+        f = torch.empty((system.N, 2, L), dtype=torch.float64, device=dev)
+        J = torch.empty((system.n, system.N, 2, L), dtype=torch.float64, device=dev)
+        Ab = torch.empty((system.n + 1, system.N, 2, L), dtype=torch.float64, device=dev)
+        R = torch.empty((system.n + 1, system.n + 1, 2, L), dtype=torch.float64, device=dev)
+        dx = torch.empty((system.n, 2, L), dtype=torch.float64, device=dev)
+
+        def timed(fn, prep=None):
+            for _ in range(2):
+                if prep:
+                    prep()
+                fn()
+            ms = []
+            for _ in range(reps):
+                flush.zero_()
+                if prep:
+                    prep()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                torch.cuda.synchronize()
+                ms.append(a.elapsed_time(b))
+            return statistics.median(ms)
+
+        t_eval = timed(lambda: S.eval(prec, x, f, J))
+        Ab0 = torch.cat([J, -f[None]], 0).contiguous()
+
+        def prep_ab():
+            Ab.copy_(Ab0)
+
+        t_ls = timed(lambda: S.lstsq(prec, Ab, R, dx), prep_ab)
+        x0 = torch.tensor(system.point("x0", L), device=dev)
+        t_step = timed(lambda: S.newton(prec, x, 1), lambda: x.copy_(x0))
+        ev_ops, ls_ops = algorithmic_fp64(system, L)
+        out["eval_diff"][prec] = {"monomials_per_s": system.T / (t_eval / 1e3), "ms": t_eval,
+                                  "fp64_ginstr_per_s": ev_ops / (t_eval / 1e3) / 1e9}
+        out["lstsq_ms"][prec] = t_ls
+        out["newton_step_ms"][prec] = t_step
+        if prec == args.prec:
+            achieved = ls_ops / (t_ls / 1e3) / 1e9
+            roof = {"kernel": "MGS least squares (k_mgs_pivot, k_mgs_update, k_backsub)",
+                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
+                    "unit": "G FP64 instr/s", "frac": achieved / FP64_PEAK_GINSTR,
+                    "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz",
+                    "traffic": None,
+                    "algorithmic_fp64_instr": ls_ops}
+    return out, roof
+
+
+if __name__ == "__main__":
+    sys.exit(main())

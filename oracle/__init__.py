@@ -165,7 +165,7 @@ def mgs(A, L: int, nthreads: int = 1):
     """
     A = _f64(A)
     m, ncols = A.shape[0], A.shape[1]
-    Acm = np.ascontiguousarray(A.transpose(1, 0, 2, 3))
+    Acm = np.array(A.transpose(1, 0, 2, 3), order="C", copy=True)  # never alias the input
     Rcm = np.zeros((ncols, ncols, 2, L))
     st = lib().o_mgs(L, m, ncols, _p(Acm), m, _p(Rcm), ncols, nthreads)
     if st:
@@ -179,7 +179,7 @@ def backsub(R, L: int):
     R = _f64(R)
     ncols = R.shape[0]
     n = ncols - 1
-    Rcm = np.ascontiguousarray(R.transpose(1, 0, 2, 3))
+    Rcm = np.array(R.transpose(1, 0, 2, 3), order="C", copy=True)
     x = np.zeros((max(n, 1), 2, L))
     st = lib().o_backsub(L, n, _p(Rcm), ncols, _p(x))
     if st:

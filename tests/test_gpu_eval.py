@@ -63,7 +63,7 @@ def test_edge_cases(prec, L):
         inputs.random_system(1, 1, 3, 1, 7, seed=1),
         inputs.random_system(3, 3, (1, 4), (1, 3), 4, seed=2, constant=False),
         inputs.random_system(6, 5, (0, 3), (1, 5), 3, seed=3),
-        inputs.random_system(4, 48, 5, (30, 40), 3, seed=4),
+        inputs.random_system(48, 48, 2, (30, 40), 3, seed=4),
         inputs.random_system(5, 4, 6, 1, 5, seed=5),
     ]
     # a variable that appears in no term: a zero Jacobian column

@@ -97,7 +97,8 @@ def test_newton_gn32_parity(prec, L):
         d[:, :, 0] -= s.xstar
         errs.append(float(limb_diff(d, np.zeros_like(d)).max()))
         fo_norm = float(np.sqrt((fo[:, :, 0] ** 2).sum()))
-        assert abs(rep["res_norm"][0] - fo_norm) <= 1e-10 * fo_norm + 1e-300
+        # at the precision floor f is rounding noise of size ~ tol * (term scale)
+        assert abs(rep["res_norm"][0] - fo_norm) <= 1e-10 * fo_norm + 100 * tol
     assert errs[-1] <= tol
     assert errs[1] <= max(1e4 * errs[0] ** 2, tol)
     sysg.close()
