@@ -59,9 +59,8 @@ def algorithmic_fp64(system, L):
 
     c = FP64_COST[L]
     k = np.diff(system.mono_ptr)
-    ell = np.add.reduceat((system.exp >= 2).astype(np.int64), system.mono_ptr[:-1]) \
-        if system.nnz else np.zeros_like(k)
-    ell = np.where(k > 0, ell, 0)
+    cs = np.concatenate([[0], np.cumsum(system.exp >= 2)])
+    ell = cs[system.mono_ptr[1:]] - cs[system.mono_ptr[:-1]]
     mults = np.where(k >= 2, 3 * k - 3, np.where(k == 1, 1, 0)) + ell
     pmax = max(int(system.exp.max()) - 1, 1)
     eval_ops = int(mults.sum()) * c["mul"] + int(k.sum()) * c["scale"]
