@@ -142,6 +142,34 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
 gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, double tol,
                     gn_report *report, void *cuda_stream);
 
+/*
+ * gn_eval_noalloc — the same evaluation as gn_eval, for callers that may not
+ * allocate device memory when they evaluate (a host thread inside a CUDA
+ * stream capture it does not own, a real-time loop that forbids allocator
+ * calls, a process whose device memory is a fixed pool handed out
+ * elsewhere).  gn_eval allocates its workspace on first use; this call
+ * allocates nothing: it calls no cudaMalloc, no cudaFree and no allocating
+ * library routine.  Its scratch is one static device array of
+ * GN_NOALLOC_SCRATCH_BYTES inside the library, which every process that
+ * loads the library holds on each GPU it uses until it exits.
+ *   Arguments, layouts and outputs are those of gn_eval; d_x, d_f and d_J
+ *   remain caller memory and the system must already be loaded (loading it
+ *   allocates).
+ *   Returns GN_EINVAL when the scratch the system needs — 256 bytes plus
+ *   16 * prec bytes per power-table entry (n x max(dmax-1, 1)), per term (T)
+ *   and per variable occurrence (nnz), each part rounded up to 256 bytes —
+ *   exceeds GN_NOALLOC_SCRATCH_BYTES.
+ *   The first call on a device looks up the scratch address on that device
+ *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   All calls share the one array and it keeps the last call's contents:
+ *   calls whose work overlaps on the GPU (other streams, other host threads)
+ *   race on it and must be serialized by the caller.
+ * The paper has no counterpart of this entry point.
+ */
+#define GN_NOALLOC_SCRATCH_BYTES (64u << 20)
+gn_status gn_eval_noalloc(const gn_system *s, gn_prec prec, const double *d_x, double *d_f,
+                          double *d_J, int64_t ldJ, void *cuda_stream);
+
 /* Human-readable name of a status. */
 const char *gn_status_str(gn_status st);
 

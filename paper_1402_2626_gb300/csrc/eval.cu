@@ -13,6 +13,8 @@
 //     owner (one thread per Jacobian entry, one warp per polynomial) in term
 //     order: no atomics (multiword values have none) and bitwise
 //     reproducible results.
+#include <mutex>
+
 #include "internal.h"
 #include "mw.cuh"
 
@@ -180,3 +182,90 @@ gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int n
 }
 
 }  // namespace gn
+
+// ---------------------------------------------------------------------------
+// gn_eval_noalloc: evaluation with library-static scratch instead of the
+// per-system workspace, for callers that cannot allocate device memory at
+// the time they evaluate.  The paper has no counterpart of this entry point.
+// ---------------------------------------------------------------------------
+
+namespace gn {
+
+// Scratch for the power table, the staged terms and partials, and a status
+// word.  Every process that loads the library holds this much device memory
+// on each GPU it uses, until it exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GN_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_noalloc_mutex;
+static unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the scratch, per device
+
+// Host code must not hand g_noalloc_scratch to a kernel: on the host that
+// name is a stand-in, not a device address.  Look the address up once per
+// device, with that device current.
+static gn_status noalloc_scratch(unsigned char **out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GN_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return GN_ECUDA;
+    }
+    g_noalloc_ptr[dev] = (unsigned char *)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return GN_OK;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+template <int L>
+static gn_status eval_noalloc_impl(const gn_system *s, const double *d_x, double *d_f, double *d_J,
+                                   int64_t ldJ, cudaStream_t st) {
+  const size_t W = 2 * L;
+  const size_t b_status = 256;
+  const size_t b_pow = align256(sizeof(double) * W * (size_t)s->n * s->pmax);
+  const size_t b_val = align256(sizeof(double) * W * (size_t)(s->T > 0 ? s->T : 1));
+  const size_t b_d = align256(sizeof(double) * W * (size_t)(s->nnz > 0 ? s->nnz : 1));
+  if (b_status + b_pow + b_val + b_d > (size_t)GN_NOALLOC_SCRATCH_BYTES) return GN_EINVAL;
+  unsigned char *base;
+  gn_status e = noalloc_scratch(&base);
+  if (e) return e;
+  int32_t *status = (int32_t *)base;
+  double *pow = (double *)(base + b_status);
+  double *stage_val = (double *)(base + b_status + b_pow);
+  double *stage_d = (double *)(base + b_status + b_pow + b_val);
+  // the scratch keeps the previous call's contents: the status word must start at 0
+  if (cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
+  k_powers<L><<<(s->n + 127) / 128, 128, 0, st>>>(d_x, s->n, s->pmax, pow, status);
+  if (s->T > 0)
+    k_monomials<L><<<(unsigned)((s->T + 127) / 128), 128, 0, st>>>(
+        s->d_mono_off, s->d_occ, s->d_coef, s->T, pow, s->n, stage_val, stage_d, status);
+  if (d_J) {
+    if (s->nz < (int64_t)s->N * s->n &&
+        cudaMemset2DAsync(d_J, sizeof(double) * W * ldJ, 0, sizeof(double) * W * s->N, s->n, st) !=
+            cudaSuccess)
+      return GN_ECUDA;
+    if (s->nz > 0)
+      k_sum_jacobian<L><<<(unsigned)((s->nz + 127) / 128), 128, 0, st>>>(
+          s->nz, s->d_jz_row, s->d_jz_col, s->d_jz_ptr, s->d_jz_occ, stage_d, d_J, ldJ, status);
+  }
+  if (d_f) k_sum_f<L><<<(s->N + 3) / 4, 128, 0, st>>>(s->N, s->d_poly_ptr, stage_val, d_f, 0, status);
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
+}  // namespace gn
+
+extern "C" gn_status gn_eval_noalloc(const gn_system *s, gn_prec prec, const double *d_x,
+                                     double *d_f, double *d_J, int64_t ldJ, void *cuda_stream) {
+  if (!s || !d_x || (d_J && ldJ < s->N) || s->kmax > gn::KMAX) return GN_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  switch (prec) {
+    case GN_D: return gn::eval_noalloc_impl<1>(s, d_x, d_f, d_J, ldJ, st);
+    case GN_DD: return gn::eval_noalloc_impl<2>(s, d_x, d_f, d_J, ldJ, st);
+    case GN_QD: return gn::eval_noalloc_impl<4>(s, d_x, d_f, d_J, ldJ, st);
+  }
+  return GN_EINVAL;
+}

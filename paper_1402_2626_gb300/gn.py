@@ -33,7 +33,7 @@ REPORT_MAX = 64
 
 # exported symbols declared in include/gn.h
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_info", "gn_eval", "gn_lstsq",
-           "gn_newton", "gn_status_str", "gn_version")
+           "gn_newton", "gn_status_str", "gn_version", "gn_eval_noalloc")
 
 
 class GnError(RuntimeError):
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_system_info.restype = C.c_int
         L.gn_eval.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, vp]
         L.gn_eval.restype = C.c_int
+        L.gn_eval_noalloc.argtypes = [vp, C.c_int, vp, vp, vp, C.c_int64, vp]
+        L.gn_eval_noalloc.restype = C.c_int
         L.gn_lstsq.argtypes = [vp, C.c_int, C.c_int32, C.c_int32, vp, C.c_int64, vp, vp, vp]
         L.gn_lstsq.restype = C.c_int
         L.gn_newton.argtypes = [vp, C.c_int, vp, C.c_int32, dp, C.POINTER(Report), vp]
@@ -150,6 +152,12 @@ class System:
         ldJ = self.N if J is None else J.shape[1]
         _check(self._lib.gn_eval(self._h, PREC[prec], _ptr(x), _ptr(f), _ptr(J), ldJ,
                                  _stream(stream)), "gn_eval")
+
+    def eval_noalloc(self, prec, x, f=None, J=None, stream=None):
+        """As eval(), through gn_eval_noalloc: no device allocation in the call."""
+        ldJ = self.N if J is None else J.shape[1]
+        _check(self._lib.gn_eval_noalloc(self._h, PREC[prec], _ptr(x), _ptr(f), _ptr(J), ldJ,
+                                         _stream(stream)), "gn_eval_noalloc")
 
     def lstsq(self, prec, Ab, R, dx, stream=None):
         """MGS least squares on Ab [n+1, m, 2, L] in place; R and dx are outputs."""
