@@ -44,6 +44,7 @@ static void ws_free(Workspace &w) {
   cudaFree(w.rinv);
   cudaFree(w.norms);
   cudaFree(w.status);
+  cudaFree(w.flags);
   if (w.h_norms) cudaFreeHost(w.h_norms);
   if (w.h_status) cudaFreeHost(w.h_status);
   w = Workspace();
@@ -65,6 +66,7 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   if (!e) e = dalloc(&w.rinv, (n + 1) * (L + 1));
   if (!e) e = dalloc(&w.norms, 3 * GN_REPORT_MAX);
   if (!e) e = dalloc(&w.status, 2);
+  if (!e) e = dalloc(&w.flags, (n + 1) * MGS_FLAGS_PER_COLUMN);
   if (!e && cudaMallocHost((void **)&w.h_norms, sizeof(double) * 3 * GN_REPORT_MAX) != cudaSuccess)
     e = GN_ENOMEM;
   if (!e && cudaMallocHost((void **)&w.h_status, sizeof(int32_t) * 2) != cudaSuccess) e = GN_ENOMEM;
@@ -74,6 +76,8 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
     ws_free(w);
     return e;
   }
+  // query cluster occupancy now: never during a stream capture
+  mgs_flow_clusters(L);
   w.ready = true;
   return GN_OK;
 }
@@ -247,21 +251,30 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   gn_status e = workspace_get(s, prec, &ws);
   if (e) return e;
   double *scratch = ws->rinv;
+  uint32_t *flags = ws->flags;
   bool own = false;
   if (n > s->n) {  // larger than the system's own workspace: temporary scratch
     if (cudaMalloc((void **)&scratch, sizeof(double) * (n + 1) * (prec + 1)) != cudaSuccess) {
       cudaGetLastError();
       return GN_ENOMEM;
     }
+    if (cudaMalloc((void **)&flags, sizeof(uint32_t) * (n + 1) * MGS_FLAGS_PER_COLUMN) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(scratch);
+      return GN_ENOMEM;
+    }
     own = true;
   }
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, d_dx, ws->status, st);
+  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, d_dx, ws->status, st);
   if (!e && cudaMemcpyAsync(ws->h_status, ws->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost,
                             st) != cudaSuccess)
     e = GN_ECUDA;
   if (!e && cudaStreamSynchronize(st) != cudaSuccess) e = GN_ECUDA;
-  if (own) cudaFree(scratch);
+  if (own) {
+    cudaFree(scratch);
+    cudaFree(flags);
+  }
   if (e) return e;
   return (gn_status)ws->h_status[0];
 }
@@ -277,7 +290,7 @@ static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cu
   const int32_t N = s->N, n = s->n;
   gn_status e = launch_eval(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
   if (e) return e;
-  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->dx, ws->status, st);
+  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->dx, ws->status, st);
   if (e) return e;
   const double *fnorm = ws->rinv + (int64_t)(n + 1) * L + n;  // original norm of the b column
   return launch_update(L, n, d_x, ws->dx, fnorm, ws->norms, ws->status, st);

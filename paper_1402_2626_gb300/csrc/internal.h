@@ -20,6 +20,7 @@ struct Workspace {
   double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, then [n+1] original column norms
   double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
   int32_t *status = nullptr;    // sticky device status word
+  uint32_t *flags = nullptr;    // [(n+1) * 8] pivot publication flags of the MGS kernel
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
   // CUDA graph of one Newton step for a given x pointer and stream
@@ -57,8 +58,15 @@ gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int n
 
 // lstsq.cu
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
-                       double *d_R, double *rinv, double *d_dx, int32_t *d_status,
+                       double *d_R, double *rinv, uint32_t *flags, double *d_dx, int32_t *d_status,
                        cudaStream_t st);
+
+// mgs.cu: MGS as one launch of thread-block clusters (0 clusters: unavailable)
+int mgs_flow_clusters(int L);
+gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncols, double *R,
+                          int64_t ldr, double *rinv, uint32_t *flags, int32_t *status,
+                          cudaStream_t st);
+constexpr int MGS_FLAGS_PER_COLUMN = 8;
 gn_status launch_update(int L, int32_t n, double *d_x, const double *d_dx, const double *d_fnorm,
                         double *d_norms, int32_t *d_status, cudaStream_t st);
 
