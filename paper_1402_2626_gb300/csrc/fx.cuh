@@ -80,12 +80,19 @@ FX_HD void fx_add_to(fx<NL> &a, const fx<NL> &b, uint64_t cin = 0) {
     asm("add.cc.u64 %0, %0, %3;\n\taddc.cc.u64 %1, %1, %4;\n\taddc.u64 %2, %2, %5;"
         : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2])
         : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]));
-  } else {
-    static_assert(NL == 5, "limb count");
+  } else if constexpr (NL == 5) {
     asm("add.cc.u64 %0, %0, %5;\n\taddc.cc.u64 %1, %1, %6;\n\taddc.cc.u64 %2, %2, %7;\n\t"
         "addc.cc.u64 %3, %3, %8;\n\taddc.u64 %4, %4, %9;"
         : "+l"(a.w[0]), "+l"(a.w[1]), "+l"(a.w[2]), "+l"(a.w[3]), "+l"(a.w[4])
         : "l"(b.w[0]), "l"(b.w[1]), "l"(b.w[2]), "l"(b.w[3]), "l"(b.w[4]));
+  } else {
+    unsigned __int128 c = cin;
+    for (int i = 0; i < NL; i++) {
+      c += (unsigned __int128)a.w[i] + b.w[i];
+      a.w[i] = (uint64_t)c;
+      c >>= 64;
+    }
+    return;
   }
   if (cin) {
     if constexpr (NL == 2) {
@@ -125,7 +132,7 @@ FX_HD bool fx_add_bits(fx<NL> &a, uint64_t b, int F) {
     m >>= -s;
     s = 0;
   }
-  if (s > 64 * NL - 55) return false;
+  if (s > 64 * NL - 54) return false;  // top mantissa bit must stay below the sign bit
   const int q = s >> 6, r = s & 63;
   const uint64_t lo = m << r;
   const uint64_t hi = r ? (m >> (64 - r)) : 0;

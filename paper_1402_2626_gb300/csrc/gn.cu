@@ -63,7 +63,7 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   if (!e) e = dalloc(&w.Ab, W * N * (n + 1));
   if (!e) e = dalloc(&w.R, W * (n + 1) * (n + 1));
   if (!e) e = dalloc(&w.dx, W * n);
-  if (!e) e = dalloc(&w.rinv, (n + 1) * (L + 1));
+  if (!e) e = dalloc(&w.rinv, lstsq_scratch_doubles(s->n, L));
   if (!e) e = dalloc(&w.norms, 3 * GN_REPORT_MAX);
   if (!e) e = dalloc(&w.status, 2);
   if (!e) e = dalloc(&w.flags, (n + 1) * MGS_FLAGS_PER_COLUMN);
@@ -254,7 +254,7 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   uint32_t *flags = ws->flags;
   bool own = false;
   if (n > s->n) {  // larger than the system's own workspace: temporary scratch
-    if (cudaMalloc((void **)&scratch, sizeof(double) * (n + 1) * (prec + 1)) != cudaSuccess) {
+    if (cudaMalloc((void **)&scratch, sizeof(double) * lstsq_scratch_doubles(n, prec)) != cudaSuccess) {
       cudaGetLastError();
       return GN_ENOMEM;
     }
@@ -266,7 +266,7 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
     own = true;
   }
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, d_dx, ws->status, st);
+  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, d_dx, ws->status, st, true);
   if (!e && cudaMemcpyAsync(ws->h_status, ws->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost,
                             st) != cudaSuccess)
     e = GN_ECUDA;
@@ -290,7 +290,7 @@ static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cu
   const int32_t N = s->N, n = s->n;
   gn_status e = launch_eval(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
   if (e) return e;
-  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->dx, ws->status, st);
+  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->dx, ws->status, st, false);
   if (e) return e;
   const double *fnorm = ws->rinv + (int64_t)(n + 1) * L + n;  // original norm of the b column
   return launch_update(L, n, d_x, ws->dx, fnorm, ws->norms, ws->status, st);

@@ -1,0 +1,211 @@
+// ifx.cuh — signed multiword integer products for block-floating-point
+// linear algebra on the integer pipe.
+//
+// Modified Gram-Schmidt (Section 3) runs with one binary exponent per column
+// and K-limb two's-complement integer mantissas per real part (K = 1, 2, 4
+// for double, double double and quad double: 62, 126 and 254 bits, more
+// than the 53, 106 and 212 bits of the floating-point formats).  A product
+// of two K-limb mantissas is formed from 64 x 64 -> 128-bit integer
+// multiplications; on GB300 these issue about 16 times faster per lane than
+// the FP64 instructions of a double-double product (and the FP64 pipe is
+// the scarce one), with a latency of a few cycles instead of 64.
+//
+// Conventions: fx<K> (fx.cuh) holds a signed value; "scale" exponents are
+// tracked by the caller.
+#pragma once
+
+#include "fx.cuh"
+
+namespace gn {
+
+typedef unsigned __int128 u128_t;
+
+template <int N>
+struct ux {
+  uint64_t w[N];
+};
+
+// |a| and the sign of a (two's complement)
+template <int K>
+FX_HD ux<K> ix_abs(const fx<K> &a, uint64_t &neg) {
+  neg = a.w[K - 1] >> 63;
+  const uint64_t m = 0 - neg;  // all ones when negative
+  ux<K> r;
+  u128_t c = neg;
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    c += (u128_t)(a.w[i] ^ m);
+    r.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return r;
+}
+
+// conditional two's-complement negation of an N-limb value
+template <int N>
+FX_HD void ix_cneg(fx<N> &a, uint64_t neg) {
+  const uint64_t m = 0 - neg;
+  u128_t c = neg;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    c += (u128_t)(a.w[i] ^ m);
+    a.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+}
+
+// Product of unsigned K-limb numbers as 2K limbs.  Exact for K <= 2; for
+// K = 4 the partial products a_i b_j with i + j < 2 are left out (they are
+// below 2^130, far under the bits the callers keep).
+template <int K>
+FX_HD ux<2 * K> ix_umul(const ux<K> &a, const ux<K> &b) {
+  ux<2 * K> p;
+#pragma unroll
+  for (int i = 0; i < 2 * K; i++) p.w[i] = 0;
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    u128_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < K; j++) {
+      if (K == 4 && i + j < 2) continue;
+      u128_t t = (u128_t)a.w[i] * b.w[j] + p.w[i + j] + carry;
+      p.w[i + j] = (uint64_t)t;
+      carry = t >> 64;
+    }
+    // propagate the row's carry
+#pragma unroll
+    for (int t = i + K; t < 2 * K; t++) {
+      u128_t s = (u128_t)p.w[t] + carry;
+      p.w[t] = (uint64_t)s;
+      carry = s >> 64;
+    }
+  }
+  return p;
+}
+
+// floor(a * b / 2^(64K - 2)) for signed K-limb a, b, as K+1 limbs (signed).
+// |result| <= |a| |b| / 2^(64K-2); exact up to the K = 4 truncation above
+// (an error below one unit).
+template <int K>
+FX_HD fx<K + 1> ix_mul_shift(const fx<K> &a, const fx<K> &b) {
+  uint64_t na, nb;
+  ux<K> ua = ix_abs<K>(a, na), ub = ix_abs<K>(b, nb);
+  ux<2 * K> p = ix_umul<K>(ua, ub);
+  fx<K + 1> r;
+  // bits [64K - 2, 128K) of p: limb t = (p[K-1+t] >> 62) | (p[K+t] << 2)
+#pragma unroll
+  for (int t = 0; t <= K; t++) {
+    uint64_t lo = p.w[K - 1 + t] >> 62;
+    uint64_t hi = (K + t < 2 * K) ? (p.w[K + t] << 2) : 0;
+    r.w[t] = lo | hi;
+  }
+  ix_cneg<K + 1>(r, na ^ nb);
+  return r;
+}
+
+// |a|^2 exactly as 2K+1 limbs (unsigned, top limb zero)
+template <int K>
+FX_HD fx<2 * K + 1> ix_square(const fx<K> &a) {
+  uint64_t n;
+  ux<K> u = ix_abs<K>(a, n);
+  ux<2 * K> p;
+  if constexpr (K == 4) {
+    // exact square: all 16 partial products
+#pragma unroll
+    for (int i = 0; i < 2 * K; i++) p.w[i] = 0;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+      u128_t carry = 0;
+#pragma unroll
+      for (int j = 0; j < K; j++) {
+        u128_t t = (u128_t)u.w[i] * u.w[j] + p.w[i + j] + carry;
+        p.w[i + j] = (uint64_t)t;
+        carry = t >> 64;
+      }
+#pragma unroll
+      for (int t = i + K; t < 2 * K; t++) {
+        u128_t s = (u128_t)p.w[t] + carry;
+        p.w[t] = (uint64_t)s;
+        carry = s >> 64;
+      }
+    }
+  } else {
+    p = ix_umul<K>(u, u);
+  }
+  fx<2 * K + 1> r;
+#pragma unroll
+  for (int i = 0; i < 2 * K; i++) r.w[i] = p.w[i];
+  r.w[2 * K] = 0;
+  return r;
+}
+
+// a + b and a - b for signed N-limb values (mod 2^(64N))
+template <int N>
+FX_HD fx<N> ix_add(fx<N> a, const fx<N> &b) {
+  u128_t c = 0;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    c += (u128_t)a.w[i] + b.w[i];
+    a.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return a;
+}
+
+template <int N>
+FX_HD fx<N> ix_sub(fx<N> a, const fx<N> &b) {
+  u128_t c = 1;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    c += (u128_t)a.w[i] + (u128_t)(~b.w[i]);
+    a.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return a;
+}
+
+// the low K limbs of a signed (K+1)-limb value (caller guarantees it fits)
+template <int K>
+FX_HD fx<K> ix_narrow(const fx<K + 1> &a) {
+  fx<K> r;
+#pragma unroll
+  for (int i = 0; i < K; i++) r.w[i] = a.w[i];
+  return r;
+}
+
+// sign-extend a K-limb value to N limbs
+template <int K, int N>
+FX_HD fx<N> ix_widen(const fx<K> &a) {
+  fx<N> r;
+  const uint64_t s = 0 - (a.w[K - 1] >> 63);
+#pragma unroll
+  for (int i = 0; i < N; i++) r.w[i] = i < K ? a.w[i] : s;
+  return r;
+}
+
+// bit length of a nonnegative value (0 for zero)
+template <int N>
+FX_HD int ix_bitlen(const fx<N> &a) {
+  int p = 0;
+#pragma unroll
+  for (int i = N - 1; i >= 0; i--)
+    if (p == 0 && a.w[i]) p = 64 * i + 64 - fx_clz64(a.w[i]);
+  return p;
+}
+
+// a >> s (arithmetic) for 0 <= s < 64 N
+template <int N>
+FX_HD fx<N> ix_sar(const fx<N> &a, int s) {
+  const int q = s >> 6, r = s & 63;
+  const uint64_t sign = 0 - (a.w[N - 1] >> 63);
+  fx<N> o;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    uint64_t lo = (i + q < N) ? a.w[i + q] : sign;
+    uint64_t hi = (i + q + 1 < N) ? a.w[i + q + 1] : sign;
+    o.w[i] = r ? ((lo >> r) | (hi << (64 - r))) : lo;
+  }
+  return o;
+}
+
+}  // namespace gn

@@ -17,7 +17,7 @@ struct Workspace {
   double *Ab = nullptr;         // N x (n+1) complex, column-major, ld N
   double *R = nullptr;          // (n+1) x (n+1) complex, column-major
   double *dx = nullptr;         // [n] complex
-  double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, then [n+1] original column norms
+  double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, [n+1] original column norms, [n+1] exponents
   double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
   int32_t *status = nullptr;    // sticky device status word
   uint32_t *flags = nullptr;    // [(n+1) * 8] pivot publication flags of the MGS kernel
@@ -57,9 +57,14 @@ gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int n
                       double *d_J, int64_t ldJ, cudaStream_t st);
 
 // lstsq.cu
+// want_q: convert Q back to L-limb cascades (gn_lstsq); the Newton step skips it
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *d_dx, int32_t *d_status,
-                       cudaStream_t st);
+                       cudaStream_t st, bool want_q);
+gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_t ncols,
+                                const double *rinv, const int32_t *status, cudaStream_t st);
+// doubles of the per-solve scratch: 1/r_kk (L per column), original norms, column exponents
+inline size_t lstsq_scratch_doubles(int32_t n, int L) { return (size_t)(n + 1) * (L + 2); }
 
 // mgs.cu: MGS as one launch of thread-block clusters (0 clusters: unavailable)
 int mgs_flow_clusters(int L);

@@ -31,6 +31,7 @@
 
 #include <mutex>
 
+#include "ifx.cuh"
 #include "internal.h"
 #include "mwfx.cuh"
 
@@ -374,6 +375,12 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_flow(MfArgs a) {
   cl.sync();  // no CTA leaves while a sibling may still read its shared memory
 }
 
+}  // namespace gn
+
+#include "mgs_int.cuh"
+
+namespace gn {
+
 // Largest number of co-resident clusters for each precision, per device.
 static std::mutex g_mf_mutex;
 static int g_mf_clusters[64][5];
@@ -387,7 +394,7 @@ static int mf_max_clusters(int maxown, int ms) {
   if (slot == 0) {
     slot = -1;
     const size_t bytes = MF_SMEM_FLOOR;
-    if (cudaFuncSetAttribute(k_mgs_flow<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_mgs_int<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bytes) == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(MF_C * 64);
@@ -401,7 +408,7 @@ static int mf_max_clusters(int maxown, int ms) {
       cfg.attrs = &attr;
       cfg.numAttrs = 1;
       int n = 0;
-      if (cudaOccupancyMaxActiveClusters(&n, k_mgs_flow<L>, &cfg) == cudaSuccess && n > 0) slot = n;
+      if (cudaOccupancyMaxActiveClusters(&n, k_mgs_int<L>, &cfg) == cudaSuccess && n > 0) slot = n;
     }
     cudaGetLastError();
   }
@@ -418,11 +425,11 @@ static gn_status mf_launch(double *A, int32_t m, int64_t lda, int32_t ncols, dou
   if (maxc <= 0) return GN_ECUDA;
   const int G = maxc < ncols ? maxc : ncols;
   const int maxown = (ncols + G - 1) / G;
-  MfLayout<L> lay(maxown, ms);
+  MiLayout<L> lay(maxown, ms);
   size_t bytes = lay.bytes > MF_SMEM_FLOOR ? lay.bytes : MF_SMEM_FLOOR;
   if (bytes > 227 * 1024) return GN_EINVAL;
   if (bytes > MF_SMEM_FLOOR &&
-      cudaFuncSetAttribute(k_mgs_flow<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+      cudaFuncSetAttribute(k_mgs_int<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
           cudaSuccess)
     return GN_ECUDA;
   if (cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (size_t)ncols * MF_C, st) != cudaSuccess)
@@ -440,8 +447,17 @@ static gn_status mf_launch(double *A, int32_t m, int64_t lda, int32_t ncols, dou
   attr.val.clusterDim.z = 1;
   cfg.attrs = &attr;
   cfg.numAttrs = 1;
-  if (cudaLaunchKernelEx(&cfg, k_mgs_flow<L>, args) != cudaSuccess) return GN_ECUDA;
+  if (cudaLaunchKernelEx(&cfg, k_mgs_int<L>, args) != cudaSuccess) return GN_ECUDA;
   return GN_OK;
+}
+
+template <int L>
+static gn_status mi_to_cascade(double *A, int32_t m, int64_t lda, int32_t ncols, const double *rinv,
+                               const int32_t *status, cudaStream_t st) {
+  const double *sexp = rinv + (size_t)ncols * L + ncols;
+  dim3 grid((m + 255) / 256, ncols);
+  k_mgs_int_to_cascade<L><<<grid, 256, 0, st>>>(A, m, lda, ncols, sexp, status);
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
 int mgs_flow_clusters(int L) {
@@ -451,6 +467,16 @@ int mgs_flow_clusters(int L) {
     case 4: return mf_max_clusters<4>(0, 0);
   }
   return 0;
+}
+
+gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_t ncols,
+                                const double *rinv, const int32_t *status, cudaStream_t st) {
+  switch (L) {
+    case 1: return mi_to_cascade<1>(A, m, lda, ncols, rinv, status, st);
+    case 2: return mi_to_cascade<2>(A, m, lda, ncols, rinv, status, st);
+    case 4: return mi_to_cascade<4>(A, m, lda, ncols, rinv, status, st);
+  }
+  return GN_EINVAL;
 }
 
 gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncols, double *R,

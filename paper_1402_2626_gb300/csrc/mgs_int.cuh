@@ -1,0 +1,509 @@
+// mgs_int.cuh — the MGS kernel of mgs.cu in block floating point on the
+// integer pipe (included by mgs.cu).
+//
+// Column j is held in place as K-limb integer mantissas with one exponent
+// s_j (a_ij = A_ij 2^s_j, |A_ij| < 2^(64K-2), s_j from the column's original
+// norm), pivots as Q_ij = q_ij 2^(64K-2).  With K = L limbs the integer form
+// has the byte size of the L-limb floating-point form, so the conversion is
+// in place.  Per pivot k and column j:
+//   D_kj = sum_i conj(Q_ik) A_ij / 2^(64K-2)      (r_kj = D_kj 2^s_j)
+//   A_ij <- A_ij - D_kj Q_ik / 2^(64K-2)
+//   T_j  = sum_i |A_ij|^2 (exact)                 (r_jj = sqrt(T_j) 2^s_j)
+//   Q_ij = A_ij Z_j / 2^(b_j - 1),  Z_j ~ 2^(b_j + 64K - 3) / sqrt(T_j)
+// The reciprocal square root comes from the double rsqrt and one or two
+// Newton steps (FP64 TwoProd pieces, exact integer sums).
+#pragma once
+
+namespace gn {
+
+// 1 / sqrt(s) for a positive cascade s of L limbs, to about 2^(-52 L)
+// relative: rsqrt seed, then Newton y <- y - y (s y^2 - 1) / 2 with the
+// residual s y^2 - 1 summed exactly (its leading bits cancel).
+template <int L>
+__device__ void rsqrt_cascade(const double (&s)[L], double (&y)[L]) {
+#pragma unroll
+  for (int l = 0; l < L; l++) y[l] = 0.0;
+  double y0 = rsqrt(s[0]);
+  if constexpr (L == 1) {
+    // one Newton step in double: y (3 - s y^2) / 2
+    double h = __fma_rn(-s[0] * y0, y0, 1.0);
+    y[0] = __fma_rn(0.5 * y0, h, y0);
+    return;
+  } else {
+    // step 1 (to ~104 bits): y1 = y0 - y0 d / 2, d = s y0^2 - 1
+    double p, e;
+    two_prod(y0, y0, p, e);
+    double d = __fma_rn(s[0], p, -1.0);
+    d = __fma_rn(s[0], e, d);
+    d = __fma_rn(s[1], p, d);
+    double c = -0.5 * y0 * d;
+    double y1h, y1l;
+    fast_two_sum(y0, c, y1h, y1l);
+    if constexpr (L == 2) {
+      y[0] = y1h;
+      y[1] = y1l;
+      return;
+    } else {
+      // step 2 (to ~208 bits) with exact sums: d = s y1^2 - 1, y2 = y1 - y1 d / 2
+      constexpr int NL = 5;
+      const int F = 290;  // values near 1
+      double q[4] = {y1h, y1l, 0.0, 0.0};
+      fx<NL> acc;
+      fx_zero<NL>(acc);
+      fx_add_prod<4, NL>(acc, q, q, false, F);
+      double y2c[4];
+      fx_to_cascade<NL, 4>(acc, F, y2c);  // y1^2
+      fx_zero<NL>(acc);
+      fx_add_prod<4, NL>(acc, s, y2c, false, F);
+      fx_add_bits<NL>(acc, fx_dbits(1.0) ^ 0x8000000000000000ull, F);
+      double dd[4];
+      fx_to_cascade<NL, 4>(acc, F, dd);  // d ~ 2^-104, about 186 bits above the resolution
+      // y2 = y1 - y1 d / 2
+      fx_zero<NL>(acc);
+      fx_add_limbs<4, NL>(acc, q, false, F);
+      double hd[4] = {0.5 * dd[0], 0.5 * dd[1], 0.5 * dd[2], 0.5 * dd[3]};
+      fx_add_prod<4, NL>(acc, q, hd, true, F);
+      fx_to_cascade<NL, 4>(acc, F, y);
+    }
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
+  constexpr int K = L;          // limbs per real mantissa
+  constexpr int W = 2 * L;      // doubles (= 64-bit words) per complex entry
+  constexpr int S = 64 * K - 2; // scale of the pivot columns Q
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int g = blockIdx.x / MF_C;
+  const int G = a.G;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = a.m, ncols = a.ncols;
+  const int ms = (m + MF_C - 1) / MF_C;
+  const int i0 = min(m, rank * ms), i1 = min(m, i0 + ms);
+  const int no = (g < ncols) ? (ncols - g + G - 1) / G : 0;
+
+  // shared memory
+  int *sS = (int *)smem;                                   // [maxown] column exponents s_j
+  double *sN0 = (double *)(smem + 16 * ((a.maxown * 4 + 15) / 16));  // [maxown]
+  double *sN0p = sN0 + a.maxown;                           // [maxown]
+  fx<K + 1> *sDot = (fx<K + 1> *)(sN0p + a.maxown);        // [2][maxown][2] bulk partials
+  fx<K + 1> *sCritD = sDot + 4 * a.maxown;                 // [2] critical dot partial
+  fx<2 * K + 1> *sCritT = (fx<2 * K + 1> *)(sCritD + 2);   // [1] critical norm partial
+  fx<K + 1> *sWarpD = (fx<K + 1> *)(sCritT + 1);           // [MF_WARPS][2]
+  fx<2 * K + 1> *sWarpT = (fx<2 * K + 1> *)(sWarpD + 2 * MF_WARPS);  // [MF_WARPS]
+  fx<K> *sR = (fx<K> *)(sWarpT + MF_WARPS);                // [maxown + 1][2] r_kj mantissas
+  fx<K> *sQ = sR + 2 * (a.maxown + 1);                     // [ms][2] pivot slice
+  int *sOk = (int *)(sQ + 2 * (ms > 0 ? ms : 1));
+  int *sAccept = sOk + 1;
+  int *sB = sOk + 2;                                       // b_j of the pivot
+  fx<K> *sZ = (fx<K> *)(sOk + 4);                          // normalisation multiplier
+  bool ok = true;
+
+  auto col = [&](int j) { return (fx<K> *)(a.A + (int64_t)j * a.lda * W); };
+
+  // original column norms (double), exponents, conversion to mantissas in place
+  for (int c = warp; c < no; c += MF_WARPS) {
+    const double *cp = a.A + (int64_t)(g + G * c) * a.lda * W;
+    double s = 0.0;
+    for (int i = i0 + lane; i < i1; i += 32) {
+      double re = cp[(int64_t)i * W], im = cp[(int64_t)i * W + L];
+      s = fma(re, re, fma(im, im, s));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sN0p[c] = s;
+  }
+  cl.sync();
+  for (int c = tid; c < no; c += MF_THREADS) {
+    double t = 0.0;
+    for (int r = 0; r < MF_C; r++) t += cl.map_shared_rank(sN0p, r)[c];
+    const double n0 = sqrt(t);
+    sN0[c] = n0;
+    const int sj = fx_exponent_of(n0 * 1.0000001 + 1e-300) - S;
+    sS[c] = sj;
+    if (rank == 0) {
+      a.nrm0[g + G * c] = n0;
+      a.nrm0[ncols + g + G * c] = (double)sj;
+    }
+  }
+  __syncthreads();
+  for (int c = warp; c < no; c += MF_WARPS) {
+    double *cp = a.A + (int64_t)(g + G * c) * a.lda * W;
+    const int F = -sS[c];
+    for (int i = i0 + lane; i < i1; i += 32) {
+      double *e = cp + (int64_t)i * W;
+      fx<K> re, im;
+      fx_zero<K>(re);
+      fx_zero<K>(im);
+#pragma unroll
+      for (int l = 0; l < L; l++) {
+        ok &= fx_add_double<K>(re, e[l], F);
+        ok &= fx_add_double<K>(im, e[L + l], F);
+      }
+      fx<K> *d = (fx<K> *)e;
+      d[0] = re;
+      d[1] = im;
+    }
+  }
+  __syncthreads();
+
+  // Exact sum over the cluster of one value per CTA held by thread 0:
+  // every CTA gets the total (in thread 0).  slot is this CTA's smem copy.
+  // (Called by all threads of all CTAs of the cluster.)
+
+  // pivot j (norm, rank test, normalisation, publication); 2 threads per row
+  auto pivot = [&](int j, int c) {
+    fx<K> *aj = col(j);
+    const int sj = sS[c];
+    fx<2 * K + 1> t;
+    fx_zero<2 * K + 1>(t);
+    for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
+      const int i = i0 + (e >> 1), part = e & 1;
+      t = ix_add<2 * K + 1>(t, ix_square<K>(aj[2 * i + part]));
+    }
+    // CTA sum
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fx<2 * K + 1> u;
+#pragma unroll
+      for (int w = 0; w < 2 * K + 1; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, t.w[w], o);
+      t = ix_add<2 * K + 1>(t, u);
+    }
+    __syncthreads();
+    if (lane == 0) sWarpT[warp] = t;
+    __syncthreads();
+    if (tid == 0) {
+      for (int w = 1; w < MF_WARPS; w++) t = ix_add<2 * K + 1>(t, sWarpT[w]);
+      *sCritT = t;
+    }
+    cl.sync();
+    if (tid == 0) {
+      fx<2 * K + 1> T;
+      fx_zero<2 * K + 1>(T);
+      for (int r = 0; r < MF_C; r++) T = ix_add<2 * K + 1>(T, *cl.map_shared_rank(sCritT, r));
+      double sc[L];
+      fx_to_cascade<2 * K + 1, L>(T, -2 * sj, sc);  // ||a_j||^2
+      int accept = 1;
+      const int bl = ix_bitlen<2 * K + 1>(T);
+      const int b = (bl + 1) >> 1;  // ||A|| < 2^b
+      double rinv[L];
+      if (bl == 0) {
+        accept = 0;
+#pragma unroll
+        for (int l = 0; l < L; l++) rinv[l] = 0.0;
+      } else {
+        rsqrt_cascade<L>(sc, rinv);
+      }
+      // r_jj = ||a_j|| = s * rinv
+      double rjj[L];
+      {
+        constexpr int NL = FxCfg<L>::NL;
+        fx<NL> acc;
+        fx_zero<NL>(acc);
+        const int E = (fx_exponent_of(sc[0]) + 1) / 2 + 1;
+        ok &= fx_add_prod<L, NL>(acc, sc, rinv, false, FxCfg<L>::BITS - E);
+        fx_to_cascade<NL, L>(acc, FxCfg<L>::BITS - E, rjj);
+      }
+      if (!isfinite(rjj[0])) {
+        accept = 0;
+        atomicCAS(a.status, GN_OK, GN_ENONFINITE);
+      } else if (j < ncols - 1) {
+        if (!(bl > 0 && rjj[0] > ldexp(sN0[c], 8 - 50 * L))) {
+          accept = 0;
+          atomicCAS(a.status, GN_OK, GN_ESINGULAR);
+        } else if (rank == 0) {
+          for (int l = 0; l < L; l++) a.rinv[(int64_t)j * L + l] = rinv[l];
+        }
+      }
+      if (rank == 0) {
+        cx<L> rc = c_zero<L>();
+#pragma unroll
+        for (int l = 0; l < L; l++) rc.re[l] = (bl == 0) ? 0.0 : rjj[l];
+        c_store<L>(a.R + ((int64_t)j * a.ldr + j) * W, rc);
+      }
+      // Z = rinv 2^(s_j + P), P = b + 64K - 3, so Z in (2^(64K-3), 2^(64K-2)]
+      fx<K> Z;
+      fx_zero<K>(Z);
+      if (accept) {
+#pragma unroll
+        for (int l = 0; l < L; l++) ok &= fx_add_double<K>(Z, rinv[l], sj + b + 64 * K - 3);
+      }
+      *sZ = Z;
+      *sB = b;
+      *sAccept = accept;
+    }
+    __syncthreads();
+    if (j < ncols - 1) {
+      if (*sAccept) {
+        const fx<K> Z = *sZ;
+        const int sh = *sB - 1;
+        uint64_t nz;
+        const ux<K> uz = ix_abs<K>(Z, nz);
+        for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
+          const int i = i0 + (e >> 1), part = e & 1;
+          uint64_t na;
+          ux<K> ua = ix_abs<K>(aj[2 * i + part], na);
+          ux<2 * K> p = ix_umul<K>(ua, uz);
+          fx<2 * K> pf;
+#pragma unroll
+          for (int w = 0; w < 2 * K; w++) pf.w[w] = p.w[w];
+          pf = ix_sar<2 * K>(pf, sh);
+          fx<K> q;
+#pragma unroll
+          for (int w = 0; w < K; w++) q.w[w] = pf.w[w];
+          ix_cneg<K>(q, na);
+          aj[2 * i + part] = q;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) st_release(a.flags + (size_t)j * MF_C + rank, *sAccept ? 1u : 2u);
+    }
+  };
+
+  if (g == 0 && no > 0) pivot(0, 0);
+
+  for (int k = 0; k < ncols - 1; k++) {
+    const int cstart = (k + 1 > g) ? (k + 1 - g + G - 1) / G : 0;
+    if (cstart >= no) break;
+    if (tid == 0) {
+      const uint32_t *f = a.flags + (size_t)k * MF_C + rank;
+      const long long t0 = clock64();
+      uint32_t v;
+      for (;;) {
+        v = ld_acquire(f);
+        if (v) break;
+        if (*(volatile int32_t *)a.status != GN_OK) {
+          v = 2;
+          break;
+        }
+        if (clock64() - t0 > MF_WAIT_CYCLES) {
+          atomicCAS(a.status, GN_OK, GN_ETIMEOUT);
+          v = 2;
+          break;
+        }
+        __nanosleep(32);
+      }
+      *sOk = (v == 1);
+    }
+    cl.sync();
+    int allok = 1;
+    for (int r = 0; r < MF_C; r++) allok &= *cl.map_shared_rank(sOk, r);
+    if (!allok) break;
+    const fx<K> *qk = col(k);
+    for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
+      const int i = i0 + (e >> 1), part = e & 1;
+      fx<K> v;
+#pragma unroll
+      for (int w = 0; w < K; w++) v.w[w] = __ldcg(&qk[2 * i + part].w[w]);
+      sQ[2 * (i - i0) + part] = v;
+    }
+    __syncthreads();
+
+    int cb = cstart;
+    const int j1 = k + 1;
+    if (j1 % G == g) {
+      // lookahead column: 2 threads per row (real part, imaginary part)
+      const int c = (j1 - g) / G;
+      fx<K> *aj = col(j1);
+      const int sj = sS[c];
+      fx<K + 1> dr, di;
+      fx_zero<K + 1>(dr);
+      fx_zero<K + 1>(di);
+      for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
+        const int i = i0 + (e >> 1), part = e & 1;
+        const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
+        const fx<K> ar = aj[2 * i], ai = aj[2 * i + 1];
+        if (part == 0) {  // Re conj(q) a = qr ar + qi ai
+          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qr, ar));
+          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qi, ai));
+        } else {  // Im conj(q) a = qr ai - qi ar
+          di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
+          di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fx<K + 1> u, v;
+#pragma unroll
+        for (int w = 0; w < K + 1; w++) {
+          u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
+          v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
+        }
+        dr = ix_add<K + 1>(dr, u);
+        di = ix_add<K + 1>(di, v);
+      }
+      __syncthreads();
+      if (lane == 0) {
+        sWarpD[2 * warp] = dr;
+        sWarpD[2 * warp + 1] = di;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int w = 1; w < MF_WARPS; w++) {
+          dr = ix_add<K + 1>(dr, sWarpD[2 * w]);
+          di = ix_add<K + 1>(di, sWarpD[2 * w + 1]);
+        }
+        sCritD[0] = dr;
+        sCritD[1] = di;
+      }
+      cl.sync();
+      if (tid == 0) {
+        fx<K + 1> tr, ti;
+        fx_zero<K + 1>(tr);
+        fx_zero<K + 1>(ti);
+        for (int r = 0; r < MF_C; r++) {
+          const fx<K + 1> *p = cl.map_shared_rank(sCritD, r);
+          tr = ix_add<K + 1>(tr, p[0]);
+          ti = ix_add<K + 1>(ti, p[1]);
+        }
+        sR[2 * a.maxown] = ix_narrow<K>(tr);
+        sR[2 * a.maxown + 1] = ix_narrow<K>(ti);
+        if (rank == 0) {
+          cx<L> rk;
+          fx_to_cascade<K + 1, L>(tr, -sj, rk.re);
+          fx_to_cascade<K + 1, L>(ti, -sj, rk.im);
+          c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
+        }
+      }
+      __syncthreads();
+      {
+        const fx<K> rr = sR[2 * a.maxown], ri = sR[2 * a.maxown + 1];
+        for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
+          const int i = i0 + (e >> 1), part = e & 1;
+          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
+          fx<K + 1> x = ix_widen<K, K + 1>(aj[2 * i + part]);
+          if (part == 0) {  // Re(a - r q) = ar - rr qr + ri qi
+            x = ix_sub<K + 1>(x, ix_mul_shift<K>(rr, qr));
+            x = ix_add<K + 1>(x, ix_mul_shift<K>(ri, qi));
+          } else {  // Im(a - r q) = ai - rr qi - ri qr
+            x = ix_sub<K + 1>(x, ix_mul_shift<K>(rr, qi));
+            x = ix_sub<K + 1>(x, ix_mul_shift<K>(ri, qr));
+          }
+          aj[2 * i + part] = ix_narrow<K>(x);
+        }
+      }
+      __syncthreads();
+      pivot(j1, c);
+      cb = c + 1;
+    }
+    const int nb = no - cb;
+    if (nb > 0) {
+      const int buf = k & 1;
+      for (int cc = warp; cc < nb; cc += MF_WARPS) {
+        const int c = cb + cc;
+        const fx<K> *aj = col(g + G * c);
+        fx<K + 1> dr, di;
+        fx_zero<K + 1>(dr);
+        fx_zero<K + 1>(di);
+        for (int i = i0 + lane; i < i1; i += 32) {
+          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
+          const fx<K> ar = aj[2 * i], ai = aj[2 * i + 1];
+          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qr, ar));
+          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qi, ai));
+          di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
+          di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          fx<K + 1> u, v;
+#pragma unroll
+          for (int w = 0; w < K + 1; w++) {
+            u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
+            v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
+          }
+          dr = ix_add<K + 1>(dr, u);
+          di = ix_add<K + 1>(di, v);
+        }
+        if (lane == 0) {
+          sDot[(buf * a.maxown + c) * 2] = dr;
+          sDot[(buf * a.maxown + c) * 2 + 1] = di;
+        }
+      }
+      cl.sync();
+      for (int cc = tid; cc < nb; cc += MF_THREADS) {
+        const int c = cb + cc;
+        fx<K + 1> tr, ti;
+        fx_zero<K + 1>(tr);
+        fx_zero<K + 1>(ti);
+        for (int r = 0; r < MF_C; r++) {
+          const fx<K + 1> *p = cl.map_shared_rank(sDot, r) + (buf * a.maxown + c) * 2;
+          tr = ix_add<K + 1>(tr, p[0]);
+          ti = ix_add<K + 1>(ti, p[1]);
+        }
+        sR[2 * c] = ix_narrow<K>(tr);
+        sR[2 * c + 1] = ix_narrow<K>(ti);
+        if (rank == 0) {
+          cx<L> rk;
+          fx_to_cascade<K + 1, L>(tr, -sS[c], rk.re);
+          fx_to_cascade<K + 1, L>(ti, -sS[c], rk.im);
+          c_store<L>(a.R + ((int64_t)(g + G * c) * a.ldr + k) * W, rk);
+        }
+      }
+      __syncthreads();
+      for (int cc = warp; cc < nb; cc += MF_WARPS) {
+        const int c = cb + cc;
+        fx<K> *aj = col(g + G * c);
+        const fx<K> rr = sR[2 * c], ri = sR[2 * c + 1];
+        for (int i = i0 + lane; i < i1; i += 32) {
+          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
+          fx<K + 1> xr = ix_widen<K, K + 1>(aj[2 * i]);
+          fx<K + 1> xi = ix_widen<K, K + 1>(aj[2 * i + 1]);
+          xr = ix_sub<K + 1>(xr, ix_mul_shift<K>(rr, qr));
+          xr = ix_add<K + 1>(xr, ix_mul_shift<K>(ri, qi));
+          xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(rr, qi));
+          xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(ri, qr));
+          aj[2 * i] = ix_narrow<K>(xr);
+          aj[2 * i + 1] = ix_narrow<K>(xi);
+        }
+      }
+    }
+  }
+  if (!ok) atomicCAS(a.status, GN_OK, GN_ENONFINITE);
+  cl.sync();
+}
+
+template <int L>
+struct MiLayout {
+  size_t bytes;
+  __host__ __device__ MiLayout(int maxown, int ms) {
+    constexpr int K = L;
+    size_t b = 16 * ((maxown * 4 + 15) / 16);
+    b += 16 * maxown;                                  // sN0, sN0p
+    b += sizeof(fx<K + 1>) * (4 * maxown + 2);         // sDot, sCritD
+    b += sizeof(fx<2 * K + 1>);                        // sCritT
+    b += sizeof(fx<K + 1>) * 2 * MF_WARPS;             // sWarpD
+    b += sizeof(fx<2 * K + 1>) * MF_WARPS;             // sWarpT
+    b += sizeof(fx<K>) * 2 * (maxown + 1);             // sR
+    b += sizeof(fx<K>) * 2 * (ms > 0 ? ms : 1);        // sQ
+    b += 16 + sizeof(fx<K>) + 64;                      // flags, Z, slack
+    bytes = (b + 255) & ~(size_t)255;
+  }
+};
+
+// Q (and the residual b - Q y) back from mantissas to L-limb cascades:
+// column j < n at scale 2^-(64K-2), the last column at 2^s_n.
+template <int L>
+__global__ void k_mgs_int_to_cascade(double *A, int32_t m, int64_t lda, int32_t ncols,
+                                     const double *sexp, const int32_t *status) {
+  constexpr int K = L, W = 2 * L;
+  if (*status != GN_OK) return;
+  const int j = blockIdx.y;
+  const int F = (j < ncols - 1) ? (64 * K - 2) : -(int)sexp[j];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    double *e = A + ((int64_t)j * lda + i) * W;
+    fx<K> *v = (fx<K> *)e;
+    fx<K> re = v[0], im = v[1];
+    double cr[L], ci[L];
+    fx_to_cascade<K, L>(re, F, cr);
+    fx_to_cascade<K, L>(im, F, ci);
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+      e[l] = cr[l];
+      e[L + l] = ci[l];
+    }
+  }
+}
+
+}  // namespace gn

@@ -1,0 +1,49 @@
+// Host harness for csrc/ifx.cuh (test support).  Reads lines
+// "op K a_0..a_{K-1} b_0..b_{K-1} [s]" (hex limbs, little-endian) and prints
+// the result limbs in hex.  ops: mul (ix_mul_shift), sq (ix_square),
+// add, sub, sar (by s), bitlen.
+#include <cstdio>
+#include <cstring>
+#include <cstdint>
+#include "../paper_1402_2626_gb300/csrc/ifx.cuh"
+
+template <int K>
+static void run(const char *op) {
+  gn::fx<K> a, b;
+  for (int i = 0; i < K; i++) scanf("%llx", (unsigned long long *)&a.w[i]);
+  for (int i = 0; i < K; i++) scanf("%llx", (unsigned long long *)&b.w[i]);
+  int s = 0;
+  if (!strcmp(op, "sar")) scanf("%d", &s);
+  if (!strcmp(op, "mul")) {
+    gn::fx<K + 1> r = gn::ix_mul_shift<K>(a, b);
+    for (int i = 0; i < K + 1; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "sq")) {
+    gn::fx<2 * K + 1> r = gn::ix_square<K>(a);
+    for (int i = 0; i < 2 * K + 1; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "add")) {
+    gn::fx<K> r = gn::ix_add<K>(a, b);
+    for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "sub")) {
+    gn::fx<K> r = gn::ix_sub<K>(a, b);
+    for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "sar")) {
+    gn::fx<K> r = gn::ix_sar<K>(a, s);
+    for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "bitlen")) {
+    printf("%x ", gn::ix_bitlen<K>(a));
+  }
+  printf("\n");
+}
+
+int main() {
+  char op[16];
+  int K;
+  while (scanf("%15s %d", op, &K) == 2) {
+    if (K == 1) run<1>(op);
+    else if (K == 2) run<2>(op);
+    else if (K == 4) run<4>(op);
+    else return 2;
+    fflush(stdout);
+  }
+  return 0;
+}

@@ -1,0 +1,97 @@
+"""Host-side pins of the block-floating-point integer products (csrc/ifx.cuh),
+checked against Python's exact big integers."""
+
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+MASK = (1 << 64) - 1
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path_factory.mktemp("ifx") / "ifx_harness")
+    subprocess.run([nvcc, "-O2", "-std=c++17", "-o", exe, os.path.join(HERE, "ifx_harness.cu")],
+                   check=True)
+    return exe
+
+
+def limbs(v, n):
+    v &= (1 << (64 * n)) - 1
+    return [(v >> (64 * i)) & MASK for i in range(n)]
+
+
+def val(ls, signed=True):
+    v = sum(x << (64 * i) for i, x in enumerate(ls))
+    n = len(ls)
+    if signed and v >> (64 * n - 1):
+        v -= 1 << (64 * n)
+    return v
+
+
+def run(exe, lines):
+    out = subprocess.run([exe], input="\n".join(lines) + "\n", capture_output=True, text=True,
+                         check=True).stdout.strip().splitlines()
+    return [[int(h, 16) for h in line.split()] for line in out]
+
+
+def rand_signed(rng, K, bits=None):
+    bits = bits if bits is not None else 64 * K - 2
+    mag = int(rng.integers(0, 2 ** 62)) << max(bits - 62, 0)
+    mag |= int.from_bytes(rng.bytes(8 * K), "little") & ((1 << max(bits - 62, 0)) - 1)
+    mag &= (1 << bits) - 1
+    return -mag if rng.random() < 0.5 else mag
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_mul_shift(harness, K):
+    rng = np.random.default_rng(K)
+    cases = []
+    for _ in range(300):
+        a = rand_signed(rng, K, int(rng.integers(1, 64 * K - 1)))
+        b = rand_signed(rng, K, int(rng.integers(1, 64 * K - 1)))
+        cases.append((a, b))
+    cases += [(0, 5), (-(1 << (64 * K - 2)), 1 << (64 * K - 2)), (1, -1)]
+    lines = [f"mul {K} " + " ".join("%x" % x for x in limbs(a, K) + limbs(b, K)) for a, b in cases]
+    for (a, b), got in zip(cases, run(harness, lines)):
+        exact = a * b
+        want = abs(exact) >> (64 * K - 2)
+        want = -want if exact < 0 else want
+        g = val(got)
+        slack = 1 if K < 4 else 2  # K = 4 leaves out the lowest partial products
+        assert abs(g - want) <= slack, (K, a, b, g, want)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_square_add_sub_sar_bitlen(harness, K):
+    rng = np.random.default_rng(10 + K)
+    lines, exp = [], []
+    for _ in range(200):
+        a = rand_signed(rng, K)
+        b = rand_signed(rng, K)
+        s = int(rng.integers(0, 64 * K))
+        z = [0] * K
+        lines.append(f"sq {K} " + " ".join("%x" % x for x in limbs(a, K) + z))
+        exp.append(("sq", a * a))
+        lines.append(f"add {K} " + " ".join("%x" % x for x in limbs(a, K) + limbs(b, K)))
+        exp.append(("add", val(limbs(a + b, K))))
+        lines.append(f"sub {K} " + " ".join("%x" % x for x in limbs(a, K) + limbs(b, K)))
+        exp.append(("sub", val(limbs(a - b, K))))
+        lines.append(f"sar {K} " + " ".join("%x" % x for x in limbs(a, K) + z) + f" {s}")
+        exp.append(("sar", a >> s))
+        lines.append(f"bitlen {K} " + " ".join("%x" % x for x in limbs(abs(a), K) + z))
+        exp.append(("bitlen", abs(a).bit_length()))
+    for (kind, want), got in zip(exp, run(harness, lines)):
+        if kind == "sq":
+            assert val(got, signed=False) == want
+        elif kind == "bitlen":
+            assert got[0] == want
+        else:
+            assert val(got) == want, kind
