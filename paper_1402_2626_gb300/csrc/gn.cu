@@ -45,6 +45,8 @@ static void ws_free(Workspace &w) {
   cudaFree(w.norms);
   cudaFree(w.status);
   cudaFree(w.flags);
+  cudaFree(w.Rm);
+  cudaFree(w.Zs);
   if (w.h_norms) cudaFreeHost(w.h_norms);
   if (w.h_status) cudaFreeHost(w.h_status);
   w = Workspace();
@@ -67,6 +69,8 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   if (!e) e = dalloc(&w.norms, 3 * GN_REPORT_MAX);
   if (!e) e = dalloc(&w.status, 2);
   if (!e) e = dalloc(&w.flags, (n + 1) * MGS_FLAGS_PER_COLUMN);
+  if (!e) e = dalloc(&w.Rm, W * (n + 1) * (n + 1));
+  if (!e) e = dalloc(&w.Zs, (n + 1) * (L + 1));
   if (!e && cudaMallocHost((void **)&w.h_norms, sizeof(double) * 3 * GN_REPORT_MAX) != cudaSuccess)
     e = GN_ENOMEM;
   if (!e && cudaMallocHost((void **)&w.h_status, sizeof(int32_t) * 2) != cudaSuccess) e = GN_ENOMEM;
@@ -252,6 +256,7 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   if (e) return e;
   double *scratch = ws->rinv;
   uint32_t *flags = ws->flags;
+  double *Rm = ws->Rm, *Zs = ws->Zs;
   bool own = false;
   if (n > s->n) {  // larger than the system's own workspace: temporary scratch
     if (cudaMalloc((void **)&scratch, sizeof(double) * lstsq_scratch_doubles(n, prec)) != cudaSuccess) {
@@ -263,10 +268,18 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
       cudaFree(scratch);
       return GN_ENOMEM;
     }
+    if (cudaMalloc((void **)&Rm, sizeof(double) * 2 * prec * (size_t)(n + 1) * (n + 1)) != cudaSuccess ||
+        cudaMalloc((void **)&Zs, sizeof(double) * (size_t)(n + 1) * (prec + 1)) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(scratch);
+      cudaFree(flags);
+      cudaFree(Rm);
+      return GN_ENOMEM;
+    }
     own = true;
   }
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, d_dx, ws->status, st, true);
+  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, Rm, Zs, d_dx, ws->status, st, true);
   if (!e && cudaMemcpyAsync(ws->h_status, ws->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost,
                             st) != cudaSuccess)
     e = GN_ECUDA;
@@ -274,6 +287,8 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   if (own) {
     cudaFree(scratch);
     cudaFree(flags);
+    cudaFree(Rm);
+    cudaFree(Zs);
   }
   if (e) return e;
   return (gn_status)ws->h_status[0];
@@ -290,7 +305,8 @@ static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cu
   const int32_t N = s->N, n = s->n;
   gn_status e = launch_eval(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
   if (e) return e;
-  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->dx, ws->status, st, false);
+  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, ws->dx,
+                   ws->status, st, false);
   if (e) return e;
   const double *fnorm = ws->rinv + (int64_t)(n + 1) * L + n;  // original norm of the b column
   return launch_update(L, n, d_x, ws->dx, fnorm, ws->norms, ws->status, st);

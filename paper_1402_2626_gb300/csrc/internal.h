@@ -21,6 +21,8 @@ struct Workspace {
   double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
   int32_t *status = nullptr;    // sticky device status word
   uint32_t *flags = nullptr;    // [(n+1) * 8] pivot publication flags of the MGS kernel
+  double *Rm = nullptr;         // mantissas of R (layout of R)
+  double *Zs = nullptr;         // [(n+1) (L+1)] mantissas and exponents of 1/r_jj
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
   // CUDA graph of one Newton step for a given x pointer and stream
@@ -59,8 +61,11 @@ gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int n
 // lstsq.cu
 // want_q: convert Q back to L-limb cascades (gn_lstsq); the Newton step skips it
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
-                       double *d_R, double *rinv, uint32_t *flags, double *d_dx, int32_t *d_status,
-                       cudaStream_t st, bool want_q);
+                       double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
+                       double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q);
+gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                             const double *rinv, double *dx, int32_t *status, cudaStream_t st);
+constexpr int BACKSUB_INT_MAX_N = 1024;
 gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_t ncols,
                                 const double *rinv, const int32_t *status, cudaStream_t st);
 // doubles of the per-solve scratch: 1/r_kk (L per column), original norms, column exponents
@@ -69,8 +74,8 @@ inline size_t lstsq_scratch_doubles(int32_t n, int L) { return (size_t)(n + 1) *
 // mgs.cu: MGS as one launch of thread-block clusters (0 clusters: unavailable)
 int mgs_flow_clusters(int L);
 gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncols, double *R,
-                          int64_t ldr, double *rinv, uint32_t *flags, int32_t *status,
-                          cudaStream_t st);
+                          int64_t ldr, double *rinv, uint32_t *flags, int32_t *status, double *Rm,
+                          double *Zs, cudaStream_t st);
 constexpr int MGS_FLAGS_PER_COLUMN = 8;
 gn_status launch_update(int L, int32_t n, double *d_x, const double *d_dx, const double *d_fnorm,
                         double *d_norms, int32_t *d_status, cudaStream_t st);

@@ -56,6 +56,8 @@ struct MfArgs {
   double *nrm0;     // [ncols] original column norms (double), written for the report
   uint32_t *flags;  // [ncols][MF_C], zero at launch
   int32_t *status;
+  double *Rm;       // r_kj mantissas (K limbs re, im) at column scale, layout of R; may be null
+  double *Zs;       // per pivot: K limbs of 1/r_jj's mantissa, then its exponent (as double)
   int32_t G;
   int32_t maxown;
 };
@@ -419,7 +421,8 @@ static int mf_max_clusters(int maxown, int ms) {
 
 template <int L>
 static gn_status mf_launch(double *A, int32_t m, int64_t lda, int32_t ncols, double *R, int64_t ldr,
-                           double *rinv, uint32_t *flags, int32_t *status, cudaStream_t st) {
+                           double *rinv, uint32_t *flags, int32_t *status, double *Rm, double *Zs,
+                           cudaStream_t st) {
   const int ms = (m + MF_C - 1) / MF_C;
   int maxc = mf_max_clusters<L>(0, ms);
   if (maxc <= 0) return GN_ECUDA;
@@ -434,7 +437,8 @@ static gn_status mf_launch(double *A, int32_t m, int64_t lda, int32_t ncols, dou
     return GN_ECUDA;
   if (cudaMemsetAsync(flags, 0, sizeof(uint32_t) * (size_t)ncols * MF_C, st) != cudaSuccess)
     return GN_ECUDA;
-  MfArgs args{A, m, lda, ncols, R, ldr, rinv, rinv + (size_t)ncols * L, flags, status, G, maxown};
+  MfArgs args{A, m, lda, ncols, R, ldr, rinv, rinv + (size_t)ncols * L, flags, status, Rm, Zs,
+              G, maxown};
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(MF_C * G);
   cfg.blockDim = dim3(MF_THREADS);
@@ -469,6 +473,30 @@ int mgs_flow_clusters(int L) {
   return 0;
 }
 
+template <int L>
+static gn_status bs_launch(const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                           const double *rinv, double *dx, int32_t *status, cudaStream_t st) {
+  const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
+  const size_t bytes = (sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 64;
+  if (bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(k_backsub_int<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess)
+    return GN_ECUDA;
+  k_backsub_int<L><<<1, BS_THREADS, bytes, st>>>(Rm, ldr, n, Zs, sexp, dx, status);
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
+gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                             const double *rinv, double *dx, int32_t *status, cudaStream_t st) {
+  if (n > BS_THREADS * BS_ROWS) return GN_EINVAL;
+  switch (L) {
+    case 1: return bs_launch<1>(Rm, ldr, n, Zs, rinv, dx, status, st);
+    case 2: return bs_launch<2>(Rm, ldr, n, Zs, rinv, dx, status, st);
+    case 4: return bs_launch<4>(Rm, ldr, n, Zs, rinv, dx, status, st);
+  }
+  return GN_EINVAL;
+}
+
 gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_t ncols,
                                 const double *rinv, const int32_t *status, cudaStream_t st) {
   switch (L) {
@@ -480,12 +508,12 @@ gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_
 }
 
 gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncols, double *R,
-                          int64_t ldr, double *rinv, uint32_t *flags, int32_t *status,
-                          cudaStream_t st) {
+                          int64_t ldr, double *rinv, uint32_t *flags, int32_t *status, double *Rm,
+                          double *Zs, cudaStream_t st) {
   switch (L) {
-    case 1: return mf_launch<1>(A, m, lda, ncols, R, ldr, rinv, flags, status, st);
-    case 2: return mf_launch<2>(A, m, lda, ncols, R, ldr, rinv, flags, status, st);
-    case 4: return mf_launch<4>(A, m, lda, ncols, R, ldr, rinv, flags, status, st);
+    case 1: return mf_launch<1>(A, m, lda, ncols, R, ldr, rinv, flags, status, Rm, Zs, st);
+    case 2: return mf_launch<2>(A, m, lda, ncols, R, ldr, rinv, flags, status, Rm, Zs, st);
+    case 4: return mf_launch<4>(A, m, lda, ncols, R, ldr, rinv, flags, status, Rm, Zs, st);
   }
   return GN_EINVAL;
 }

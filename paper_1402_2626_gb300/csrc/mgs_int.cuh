@@ -233,6 +233,12 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       *sZ = Z;
       *sB = b;
       *sAccept = accept;
+      if (rank == 0 && a.Zs && j < ncols - 1) {
+        double *zs = a.Zs + (size_t)j * (K + 1);
+#pragma unroll
+        for (int w = 0; w < K; w++) ((uint64_t *)zs)[w] = Z.w[w];
+        zs[K] = (double)(-(b + 64 * K - 3) - sj);  // 1/r_jj = Z 2^this
+      }
     }
     __syncthreads();
     if (j < ncols - 1) {
@@ -360,6 +366,11 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
         sR[2 * a.maxown] = ix_narrow<K>(tr);
         sR[2 * a.maxown + 1] = ix_narrow<K>(ti);
+        if (rank == 0 && a.Rm) {
+          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
+          rm[0] = sR[2 * a.maxown];
+          rm[1] = sR[2 * a.maxown + 1];
+        }
         if (rank == 0) {
           cx<L> rk;
           fx_to_cascade<K + 1, L>(tr, -sj, rk.re);
@@ -434,6 +445,11 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
         sR[2 * c] = ix_narrow<K>(tr);
         sR[2 * c + 1] = ix_narrow<K>(ti);
+        if (rank == 0 && a.Rm) {
+          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)(g + G * c) * a.ldr + k) * W);
+          rm[0] = sR[2 * c];
+          rm[1] = sR[2 * c + 1];
+        }
         if (rank == 0) {
           cx<L> rk;
           fx_to_cascade<K + 1, L>(tr, -sS[c], rk.re);
@@ -502,6 +518,206 @@ __global__ void k_mgs_int_to_cascade(double *A, int32_t m, int64_t lda, int32_t 
     for (int l = 0; l < L; l++) {
       e[l] = cr[l];
       e[L + l] = ci[l];
+    }
+  }
+}
+
+// Back substitution R[0:n,0:n] x = y on the mantissas the MGS kernel left
+// (Section 3, eq. 5 read as x_l = (y_l - sum_{j>l} r_lj x_j) / r_ll).
+// y is held in fixed point at the scale of the last column (K+2 limbs: two
+// limbs of headroom for intermediate growth), each x_l in block floating
+// point (K-limb mantissa per part, one exponent).  One thread per row;
+// level l: the owner of row l forms x_l = y_l / r_ll, then every row i < l
+// subtracts r_il x_l.  All integer.
+constexpr int BS_THREADS = 256;
+constexpr int BS_ROWS = 4;  // rows per thread: n <= 1024
+
+template <int L>
+__global__ void __launch_bounds__(BS_THREADS) k_backsub_int(const double *__restrict__ Rm, int64_t ldr,
+                                                            int32_t n, const double *__restrict__ Zs,
+                                                            const double *__restrict__ sexp,
+                                                            double *__restrict__ dx,
+                                                            int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, KY = K + 2;
+  __shared__ fx<K> sX[2];
+  __shared__ int sT;
+  __shared__ int sFail;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  fx<K> *sXall = (fx<K> *)bsm;                  // [n][2] mantissas of x
+  int *sTall = (int *)(sXall + 2 * (n > 0 ? n : 1));  // [n] exponents of x
+  if (*status != GN_OK) return;
+  const int tid = threadIdx.x;
+  const int sig = (int)sexp[n];  // scale of y (the last column)
+  fx<KY> Y[BS_ROWS][2];
+#pragma unroll
+  for (int p = 0; p < BS_ROWS; p++) {
+    const int i = tid + BS_THREADS * p;
+    if (i < n) {
+      const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)n * ldr + i) * W);
+      Y[p][0] = ix_widen<K, KY>(e[0]);
+      Y[p][1] = ix_widen<K, KY>(e[1]);
+    } else {
+      fx_zero<KY>(Y[p][0]);
+      fx_zero<KY>(Y[p][1]);
+    }
+  }
+  if (tid == 0) sFail = 0;
+  __syncthreads();
+  for (int l = n - 1; l >= 0; l--) {
+    const int own = l % BS_THREADS, po = l / BS_THREADS;
+    // this level's r_il, loaded before x_l is known (hides the load latency)
+    fx<K> Rr[BS_ROWS], Ri[BS_ROWS];
+#pragma unroll
+    for (int p = 0; p < BS_ROWS; p++) {
+      const int i = tid + BS_THREADS * p;
+      if (i < l) {
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)l * ldr + i) * W);
+        Rr[p] = e[0];
+        Ri[p] = e[1];
+      }
+    }
+    const int sl = (int)sexp[l];
+    if (tid == own) {
+      // x_l = y_l * 2^sig * Z 2^e
+      const double *zs = Zs + (size_t)l * (K + 1);
+      fx<K> Z;
+#pragma unroll
+      for (int w = 0; w < K; w++) Z.w[w] = ((const uint64_t *)zs)[w];
+      const int e = (int)zs[K];
+      uint64_t nz;
+      const ux<K> uz = ix_abs<K>(Z, nz);
+      fx<KY + K> P[2];
+      int B = 0;
+#pragma unroll
+      for (int part = 0; part < 2; part++) {
+        fx<KY> y;
+#pragma unroll
+        for (int q = 0; q < BS_ROWS; q++)
+          if (q == po) y = Y[q][part];
+        uint64_t ny;
+        const ux<KY> uy = ix_abs<KY>(y, ny);
+        // |y| * |Z| as KY + K limbs
+#pragma unroll
+        for (int w = 0; w < KY + K; w++) P[part].w[w] = 0;
+#pragma unroll
+        for (int a = 0; a < KY; a++) {
+          u128_t carry = 0;
+#pragma unroll
+          for (int b = 0; b < K; b++) {
+            u128_t t = (u128_t)uy.w[a] * uz.w[b] + P[part].w[a + b] + carry;
+            P[part].w[a + b] = (uint64_t)t;
+            carry = t >> 64;
+          }
+          P[part].w[a + K] = (uint64_t)carry;
+        }
+        const int bl = ix_bitlen<KY + K>(P[part]);
+        B = bl > B ? bl : B;
+        ix_cneg<KY + K>(P[part], ny ^ nz);
+      }
+      const int sh = B > 64 * K - 2 ? B - (64 * K - 2) : 0;
+      fx<K> X[2];
+#pragma unroll
+      for (int part = 0; part < 2; part++) {
+        fx<KY + K> q = ix_sar<KY + K>(P[part], sh);
+#pragma unroll
+        for (int w = 0; w < K; w++) X[part].w[w] = q.w[w];
+      }
+      sX[0] = X[0];
+      sX[1] = X[1];
+      sT = sig + e + sh;
+      sXall[2 * l] = X[0];
+      sXall[2 * l + 1] = X[1];
+      sTall[l] = sig + e + sh;
+    }
+    __syncthreads();
+    const fx<K> xr = sX[0], xi = sX[1];
+    const int t = sT;
+#pragma unroll
+    for (int p = 0; p < BS_ROWS; p++) {
+      const int i = tid + BS_THREADS * p;
+      if (i < l) {
+        const fx<K> rr = Rr[p], ri = Ri[p];
+        // r_il x_l at scale s_l + t; in units of y: shift by d = s_l + t - sig
+        const int d = sl + t - sig;
+        // re = rr xr - ri xi, im = rr xi + ri xr as 2K+1 limbs
+        fx<2 * K + 1> pr, pi;
+        {
+          uint64_t n1, n2, n3, n4;
+          ux<K> a1 = ix_abs<K>(rr, n1), b1 = ix_abs<K>(xr, n2);
+          ux<K> a2 = ix_abs<K>(ri, n3), b2 = ix_abs<K>(xi, n4);
+          ux<2 * K> p1 = ix_umul<K>(a1, b1), p2 = ix_umul<K>(a2, b2);
+          ux<2 * K> p3 = ix_umul<K>(a1, b2), p4 = ix_umul<K>(a2, b1);
+          fx<2 * K + 1> f1, f2, f3, f4;
+#pragma unroll
+          for (int w = 0; w < 2 * K; w++) {
+            f1.w[w] = p1.w[w];
+            f2.w[w] = p2.w[w];
+            f3.w[w] = p3.w[w];
+            f4.w[w] = p4.w[w];
+          }
+          f1.w[2 * K] = f2.w[2 * K] = f3.w[2 * K] = f4.w[2 * K] = 0;
+          ix_cneg<2 * K + 1>(f1, n1 ^ n2);
+          ix_cneg<2 * K + 1>(f2, n3 ^ n4);
+          ix_cneg<2 * K + 1>(f3, n1 ^ n4);
+          ix_cneg<2 * K + 1>(f4, n3 ^ n2);
+          pr = ix_sub<2 * K + 1>(f1, f2);
+          pi = ix_add<2 * K + 1>(f3, f4);
+        }
+        fx<KY> ur, ui;
+        if (d <= 0) {
+          const int s = -d;
+          if (s >= 64 * (2 * K + 1)) {
+            fx_zero<KY>(ur);
+            fx_zero<KY>(ui);
+          } else {
+            fx<2 * K + 1> qr = ix_sar<2 * K + 1>(pr, s), qi = ix_sar<2 * K + 1>(pi, s);
+#pragma unroll
+            for (int w = 0; w < KY; w++) {
+              ur.w[w] = w < 2 * K + 1 ? qr.w[w] : (0 - (qr.w[2 * K] >> 63));
+              ui.w[w] = w < 2 * K + 1 ? qi.w[w] : (0 - (qi.w[2 * K] >> 63));
+            }
+          }
+        } else {
+          // a product larger than the units of y by 2^d: only harmless when tiny
+          if (ix_bitlen<2 * K + 1>(pr) + d > 64 * KY - 2 || ix_bitlen<2 * K + 1>(pi) + d > 64 * KY - 2) sFail = 1;
+          fx_zero<KY>(ur);
+          fx_zero<KY>(ui);
+#pragma unroll
+          for (int w = 0; w < KY; w++) {
+            ur.w[w] = w < 2 * K + 1 ? pr.w[w] : (0 - (pr.w[2 * K] >> 63));
+            ui.w[w] = w < 2 * K + 1 ? pi.w[w] : (0 - (pi.w[2 * K] >> 63));
+          }
+          // shift left by d (d < 64 KY guaranteed by the check above when it succeeds)
+          const int q = d >> 6, r = d & 63;
+          fx<KY> tr = ur, ti = ui;
+#pragma unroll
+          for (int w = KY - 1; w >= 0; w--) {
+            uint64_t lo_r = (w - q >= 0) ? tr.w[w - q] : 0, lo2_r = (w - q - 1 >= 0) ? tr.w[w - q - 1] : 0;
+            uint64_t lo_i = (w - q >= 0) ? ti.w[w - q] : 0, lo2_i = (w - q - 1 >= 0) ? ti.w[w - q - 1] : 0;
+            ur.w[w] = r ? ((lo_r << r) | (lo2_r >> (64 - r))) : lo_r;
+            ui.w[w] = r ? ((lo_i << r) | (lo2_i >> (64 - r))) : lo_i;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < BS_ROWS; q++)
+          if (q == p) {
+            Y[q][0] = ix_sub<KY>(Y[q][0], ur);
+            Y[q][1] = ix_sub<KY>(Y[q][1], ui);
+          }
+      }
+    }
+    __syncthreads();
+  }
+  if (sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+  // outputs: x_l = X 2^t as L-limb cascades
+  for (int l = tid; l < n; l += BS_THREADS) {
+    double cr[L], ci[L];
+    fx_to_cascade<K, L>(sXall[2 * l], -sTall[l], cr);
+    fx_to_cascade<K, L>(sXall[2 * l + 1], -sTall[l], ci);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      dx[(int64_t)l * W + q] = cr[q];
+      dx[(int64_t)l * W + L + q] = ci[q];
     }
   }
 }
