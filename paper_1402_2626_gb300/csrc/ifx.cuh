@@ -208,4 +208,94 @@ FX_HD fx<N> ix_sar(const fx<N> &a, int s) {
   return o;
 }
 
+// Y = 2^(64K-2) / sqrt(t) for t = tt / 2^(64K) in [1/4, 1), tt a K-limb
+// unsigned fraction: FP32 reciprocal square root seed, then Newton steps
+// y <- y + y (1 - t y^2) / 2 in K-limb fixed point (precision doubles per
+// step: 24 -> 48 -> 96 -> 192 -> 384 bits).  Y is in (2^(64K-2), 2^(64K-1)].
+template <int K>
+FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
+  constexpr int S = 64 * K - 2;
+  // seed from the top 32 bits of t
+  const float tf = (float)(uint32_t)(tt.w[K - 1] >> 32) * 2.3283064365386963e-10f;  // 2^-32
+#if defined(__CUDA_ARCH__)
+  const float y0 = rsqrtf(tf);
+#else
+  const float y0 = 1.0f / __builtin_sqrtf(tf);
+#endif
+  // Y0 = y0 2^S as K limbs: y0 in (1, 2] has 24 significant bits
+  ux<K> Y;
+#pragma unroll
+  for (int i = 0; i < K; i++) Y.w[i] = 0;
+  {
+    const uint64_t m = (uint64_t)(y0 * 16777216.0f);  // y0 2^24, < 2^26
+    // place m 2^(S - 24)
+    const int sh = S - 24, q = sh >> 6, r = sh & 63;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+      uint64_t v = 0;
+      if (i == q) v = m << r;
+      if (i == q + 1 && r) v = m >> (64 - r);
+      Y.w[i] = v;
+    }
+  }
+  constexpr int ITERS = (K == 1) ? 2 : (K == 2 ? 3 : 4);
+#pragma unroll
+  for (int it = 0; it < ITERS; it++) {
+    // W = Y^2 / 2^S  (value y^2, scale 2^S), K+1 limbs
+    ux<2 * K> y2 = ix_umul<K>(Y, Y);
+    ux<K + 1> Wv;
+#pragma unroll
+    for (int t = 0; t <= K; t++) {
+      uint64_t lo = y2.w[K - 1 + t] >> 62;
+      uint64_t hi = (K + t < 2 * K) ? (y2.w[K + t] << 2) : 0;
+      Wv.w[t] = lo | hi;
+    }
+    // V = t * W = tt * W / 2^(64K)  (value t y^2 ~ 1, scale 2^S)
+    ux<K> Wk;
+#pragma unroll
+    for (int i = 0; i < K; i++) Wk.w[i] = Wv.w[i];
+    ux<2 * K> tw = ix_umul<K>(tt, Wk);  // W's top limb (<= 4 in value) handled below
+    // tw / 2^(64K): limbs K..2K-1, plus tt * Wv.w[K] (W's top limb) at weight 2^(64K)
+    ux<K> V;
+#pragma unroll
+    for (int i = 0; i < K; i++) V.w[i] = tw.w[K + i];
+    {
+      u128_t c = 0;
+#pragma unroll
+      for (int i = 0; i < K; i++) {
+        c += (u128_t)V.w[i] + (u128_t)tt.w[i] * Wv.w[K];
+        V.w[i] = (uint64_t)c;
+        c >>= 64;
+      }
+    }
+    // e = 2^S - V (signed, small), Y <- Y + Y e / 2^(S+1)
+    fx<K> one;
+#pragma unroll
+    for (int i = 0; i < K; i++) one.w[i] = (i == (S >> 6)) ? (1ull << (S & 63)) : 0;
+    fx<K> Vf;
+#pragma unroll
+    for (int i = 0; i < K; i++) Vf.w[i] = V.w[i];
+    fx<K> e = ix_sub<K>(one, Vf);
+    uint64_t ne;
+    ux<K> ue = ix_abs<K>(e, ne);
+    ux<2 * K> ye = ix_umul<K>(Y, ue);
+    // ye / 2^(S+1) = ye >> (64K - 1): limbs (K-1).. with shift 63
+    fx<K> d;
+#pragma unroll
+    for (int t = 0; t < K; t++) {
+      uint64_t lo = ye.w[K - 1 + t] >> 63;
+      uint64_t hi = (K + t < 2 * K) ? (ye.w[K + t] << 1) : 0;
+      d.w[t] = lo | hi;
+    }
+    ix_cneg<K>(d, ne);
+    fx<K> Yf;
+#pragma unroll
+    for (int i = 0; i < K; i++) Yf.w[i] = Y.w[i];
+    Yf = ix_add<K>(Yf, d);
+#pragma unroll
+    for (int i = 0; i < K; i++) Y.w[i] = Yf.w[i];
+  }
+  return Y;
+}
+
 }  // namespace gn

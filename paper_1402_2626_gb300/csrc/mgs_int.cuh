@@ -68,6 +68,72 @@ __device__ void rsqrt_cascade(const double (&s)[L], double (&y)[L]) {
   }
 }
 
+// Exact sum over the CTA, then over the cluster, of NV values of N limbs
+// held by every thread.  On return lanes 0..7 of warp 0 hold the cluster
+// totals in v.  sWarp: [MF_WARPS][NV] this CTA's scratch; sSlot: [NV] the slot
+// the cluster reads; *sOk / okv: this CTA's flag, ANDed over the cluster into
+// the return value (valid in warp 0).  Every thread of every CTA must call it.
+template <int N, int NV>
+__device__ int cluster_sum(fx<N> (&v)[NV], fx<N> *sWarp, fx<N> *sSlot, int *sOk, int okv,
+                           cg::cluster_group &cl) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      fx<N> u;
+#pragma unroll
+      for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
+      v[q] = ix_add<N>(v[q], u);
+    }
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; q++) sWarp[warp * NV + q] = v[q];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      if (lane < MF_WARPS) v[q] = sWarp[lane * NV + q];
+      else fx_zero<N>(v[q]);
+#pragma unroll
+      for (int o = 4; o > 0; o >>= 1) {
+        fx<N> u;
+#pragma unroll
+        for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
+        v[q] = ix_add<N>(v[q], u);
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < NV; q++) sSlot[q] = v[q];
+      *sOk = okv;
+    }
+  }
+  cl.sync();
+  int all = 1;
+  if (warp == 0) {
+    int okr = 1;
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      if (lane < MF_C) v[q] = cl.map_shared_rank(sSlot, lane)[q];
+      else fx_zero<N>(v[q]);
+    }
+    if (lane < MF_C) okr = *cl.map_shared_rank(sOk, lane);
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+      for (int q = 0; q < NV; q++) {
+        fx<N> u;
+#pragma unroll
+        for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
+        v[q] = ix_add<N>(v[q], u);
+      }
+    all = __all_sync(0xffffffffu, okr);
+  }
+  return all;
+}
+
 template <int L>
 __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   constexpr int K = L;          // limbs per real mantissa
@@ -95,10 +161,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   fx<2 * K + 1> *sWarpT = (fx<2 * K + 1> *)(sWarpD + 2 * MF_WARPS);  // [MF_WARPS]
   fx<K> *sR = (fx<K> *)(sWarpT + MF_WARPS);                // [maxown + 1][2] r_kj mantissas
   fx<K> *sQ = sR + 2 * (a.maxown + 1);                     // [ms][2] pivot slice
+  // wait results read by the cluster: [0,1] bulk step by parity, [2,3]
+  // lookahead step by parity, [4] the pivot's (always 1)
   int *sOk = (int *)(sQ + 2 * (ms > 0 ? ms : 1));
-  int *sAccept = sOk + 1;
-  int *sB = sOk + 2;                                       // b_j of the pivot
-  fx<K> *sZ = (fx<K> *)(sOk + 4);                          // normalisation multiplier
+  int *sAll = sOk + 5;                                     // cluster decision broadcast
+  int *sB = sOk + 6;                                       // b_j of the pivot
+  int *sAccept = sOk + 7;
+  fx<K> *sZ = (fx<K> *)(sOk + 8);                          // normalisation multiplier
+  fx<K> *sTT = sZ + 1;                                     // t of the pivot (fraction)
   bool ok = true;
 
   auto col = [&](int j) { return (fx<K> *)(a.A + (int64_t)j * a.lda * W); };
@@ -149,96 +219,61 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   }
   __syncthreads();
 
-  // Exact sum over the cluster of one value per CTA held by thread 0:
-  // every CTA gets the total (in thread 0).  slot is this CTA's smem copy.
-  // (Called by all threads of all CTAs of the cluster.)
-
-  // pivot j (norm, rank test, normalisation, publication); 2 threads per row
+  // pivot j: norm (exact), 1/||a_j|| by integer Newton, rank test,
+  // normalisation, publication; the R diagonal and 1/r_jj limbs afterwards
   auto pivot = [&](int j, int c) {
     fx<K> *aj = col(j);
     const int sj = sS[c];
-    fx<2 * K + 1> t;
-    fx_zero<2 * K + 1>(t);
+    fx<2 * K + 1> t[1];
+    fx_zero<2 * K + 1>(t[0]);
     for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
       const int i = i0 + (e >> 1), part = e & 1;
-      t = ix_add<2 * K + 1>(t, ix_square<K>(aj[2 * i + part]));
+      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * i + part]));
     }
-    // CTA sum
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fx<2 * K + 1> u;
-#pragma unroll
-      for (int w = 0; w < 2 * K + 1; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, t.w[w], o);
-      t = ix_add<2 * K + 1>(t, u);
-    }
-    __syncthreads();
-    if (lane == 0) sWarpT[warp] = t;
-    __syncthreads();
+    cluster_sum<2 * K + 1, 1>(t, sWarpT, sCritT, sOk + 4, 1, cl);
+    ux<K> Y;
+    int bl = 0, b = 0;
     if (tid == 0) {
-      for (int w = 1; w < MF_WARPS; w++) t = ix_add<2 * K + 1>(t, sWarpT[w]);
-      *sCritT = t;
-    }
-    cl.sync();
-    if (tid == 0) {
-      fx<2 * K + 1> T;
-      fx_zero<2 * K + 1>(T);
-      for (int r = 0; r < MF_C; r++) T = ix_add<2 * K + 1>(T, *cl.map_shared_rank(sCritT, r));
-      double sc[L];
-      fx_to_cascade<2 * K + 1, L>(T, -2 * sj, sc);  // ||a_j||^2
-      int accept = 1;
-      const int bl = ix_bitlen<2 * K + 1>(T);
-      const int b = (bl + 1) >> 1;  // ||A|| < 2^b
-      double rinv[L];
-      if (bl == 0) {
-        accept = 0;
-#pragma unroll
-        for (int l = 0; l < L; l++) rinv[l] = 0.0;
-      } else {
-        rsqrt_cascade<L>(sc, rinv);
-      }
-      // r_jj = ||a_j|| = s * rinv
-      double rjj[L];
+      const fx<2 * K + 1> T = t[0];
+      bl = ix_bitlen<2 * K + 1>(T);
+      b = (bl + 1) >> 1;  // sqrt(T) < 2^b
+      // rank test on ||a_j||^2 against (||a_j^0|| 2^(8-50L))^2
+      double tl[1];
+      fx_to_cascade<2 * K + 1, 1>(T, -2 * sj, tl);
+      const double th = ldexp(sN0[c], 8 - 50 * L);
+      int accept = (bl > 0) && (j == ncols - 1 || tl[0] > th * th);
+      if (!accept && j < ncols - 1) atomicCAS(a.status, GN_OK, GN_ESINGULAR);
+      // t = T / 2^(2b) in [1/4, 1) as K limbs of fraction
+      ux<K> tt;
       {
-        constexpr int NL = FxCfg<L>::NL;
-        fx<NL> acc;
-        fx_zero<NL>(acc);
-        const int E = (fx_exponent_of(sc[0]) + 1) / 2 + 1;
-        ok &= fx_add_prod<L, NL>(acc, sc, rinv, false, FxCfg<L>::BITS - E);
-        fx_to_cascade<NL, L>(acc, FxCfg<L>::BITS - E, rjj);
-      }
-      if (!isfinite(rjj[0])) {
-        accept = 0;
-        atomicCAS(a.status, GN_OK, GN_ENONFINITE);
-      } else if (j < ncols - 1) {
-        if (!(bl > 0 && rjj[0] > ldexp(sN0[c], 8 - 50 * L))) {
-          accept = 0;
-          atomicCAS(a.status, GN_OK, GN_ESINGULAR);
-        } else if (rank == 0) {
-          for (int l = 0; l < L; l++) a.rinv[(int64_t)j * L + l] = rinv[l];
-        }
-      }
-      if (rank == 0) {
-        cx<L> rc = c_zero<L>();
+        fx<2 * K + 1> sh;
+        const int d = 2 * b - 64 * K;
+        if (d >= 0) {
+          sh = ix_sar<2 * K + 1>(T, d);
+        } else {
+          // left shift by -d (T < 2^(2b) < 2^(64K))
+          const int q = (-d) >> 6, r = (-d) & 63;
 #pragma unroll
-        for (int l = 0; l < L; l++) rc.re[l] = (bl == 0) ? 0.0 : rjj[l];
-        c_store<L>(a.R + ((int64_t)j * a.ldr + j) * W, rc);
+          for (int w = 2 * K; w >= 0; w--) {
+            uint64_t lo = (w - q >= 0) ? T.w[w - q] : 0, lo2 = (w - q - 1 >= 0) ? T.w[w - q - 1] : 0;
+            sh.w[w] = r ? ((lo << r) | (lo2 >> (64 - r))) : lo;
+          }
+        }
+#pragma unroll
+        for (int w = 0; w < K; w++) tt.w[w] = sh.w[w];
       }
-      // Z = rinv 2^(s_j + P), P = b + 64K - 3, so Z in (2^(64K-3), 2^(64K-2)]
       fx<K> Z;
       fx_zero<K>(Z);
       if (accept) {
+        Y = ix_rsqrt_frac<K>(tt);  // 2^S / sqrt(t)
 #pragma unroll
-        for (int l = 0; l < L; l++) ok &= fx_add_double<K>(Z, rinv[l], sj + b + 64 * K - 3);
+        for (int w = 0; w < K; w++) Z.w[w] = (Y.w[w] >> 1) | ((w + 1 < K) ? (Y.w[w + 1] << 63) : 0);
       }
       *sZ = Z;
       *sB = b;
       *sAccept = accept;
-      if (rank == 0 && a.Zs && j < ncols - 1) {
-        double *zs = a.Zs + (size_t)j * (K + 1);
 #pragma unroll
-        for (int w = 0; w < K; w++) ((uint64_t *)zs)[w] = Z.w[w];
-        zs[K] = (double)(-(b + 64 * K - 3) - sj);  // 1/r_jj = Z 2^this
-      }
+      for (int w = 0; w < K; w++) sTT->w[w] = tt.w[w];
     }
     __syncthreads();
     if (j < ncols - 1) {
@@ -266,6 +301,39 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       __syncthreads();
       if (tid == 0) st_release(a.flags + (size_t)j * MF_C + rank, *sAccept ? 1u : 2u);
     }
+    // off the critical path: r_jj, 1/r_jj as limbs, and the pivot's mantissa for back substitution
+    if (tid == 0 && rank == 0) {
+      cx<L> rc = c_zero<L>();
+      if (bl > 0) {
+        ux<K> tt;
+#pragma unroll
+        for (int w = 0; w < K; w++) tt.w[w] = sTT->w[w];
+        if (!*sAccept) Y = ix_rsqrt_frac<K>(tt);
+        // sqrt(t) = t y: (tt Y) / 2^(64K), scale 2^S
+        ux<2 * K> ty = ix_umul<K>(tt, Y);
+        fx<K> M;
+#pragma unroll
+        for (int w = 0; w < K; w++) M.w[w] = ty.w[K + w];
+        fx_to_cascade<K, L>(M, S - b - sj, rc.re);  // r_jj = sqrt(t) 2^(b + s_j)
+        if (*sAccept && j < ncols - 1) {
+          fx<K> Yf;
+#pragma unroll
+          for (int w = 0; w < K; w++) Yf.w[w] = Y.w[w];
+          double ri[L];
+          fx_to_cascade<K, L>(Yf, S + b + sj, ri);  // 1/r_jj = y 2^-(b + s_j)
+#pragma unroll
+          for (int l = 0; l < L; l++) a.rinv[(int64_t)j * L + l] = ri[l];
+          if (a.Zs) {
+            double *zs = a.Zs + (size_t)j * (K + 1);
+            const fx<K> Z = *sZ;
+#pragma unroll
+            for (int w = 0; w < K; w++) ((uint64_t *)zs)[w] = Z.w[w];
+            zs[K] = (double)(-(b + 64 * K - 3) - sj);  // 1/r_jj = Z 2^this
+          }
+        }
+      }
+      c_store<L>(a.R + ((int64_t)j * a.ldr + j) * W, rc);
+    }
   };
 
   if (g == 0 && no > 0) pivot(0, 0);
@@ -273,6 +341,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   for (int k = 0; k < ncols - 1; k++) {
     const int cstart = (k + 1 > g) ? (k + 1 - g + G - 1) / G : 0;
     if (cstart >= no) break;
+    // wait for the rows of q_k that this CTA needs; the cluster compares
+    // notes at the step's first barrier
+    int okv = 1;
     if (tid == 0) {
       const uint32_t *f = a.flags + (size_t)k * MF_C + rank;
       const long long t0 = clock64();
@@ -291,12 +362,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
         __nanosleep(32);
       }
-      *sOk = (v == 1);
+      okv = (v == 1);
     }
-    cl.sync();
-    int allok = 1;
-    for (int r = 0; r < MF_C; r++) allok &= *cl.map_shared_rank(sOk, r);
-    if (!allok) break;
+    __syncthreads();
     const fx<K> *qk = col(k);
     for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
       const int i = i0 + (e >> 1), part = e & 1;
@@ -309,76 +377,36 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
 
     int cb = cstart;
     const int j1 = k + 1;
+    int allok = 1;
     if (j1 % G == g) {
       // lookahead column: 2 threads per row (real part, imaginary part)
       const int c = (j1 - g) / G;
       fx<K> *aj = col(j1);
       const int sj = sS[c];
-      fx<K + 1> dr, di;
-      fx_zero<K + 1>(dr);
-      fx_zero<K + 1>(di);
+      fx<K + 1> d2[2];
+      fx_zero<K + 1>(d2[0]);
+      fx_zero<K + 1>(d2[1]);
       for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
         const int i = i0 + (e >> 1), part = e & 1;
         const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
         const fx<K> ar = aj[2 * i], ai = aj[2 * i + 1];
         if (part == 0) {  // Re conj(q) a = qr ar + qi ai
-          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qr, ar));
-          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qi, ai));
+          d2[0] = ix_add<K + 1>(d2[0], ix_mul_shift<K>(qr, ar));
+          d2[0] = ix_add<K + 1>(d2[0], ix_mul_shift<K>(qi, ai));
         } else {  // Im conj(q) a = qr ai - qi ar
-          di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
-          di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
+          d2[1] = ix_add<K + 1>(d2[1], ix_mul_shift<K>(qr, ai));
+          d2[1] = ix_sub<K + 1>(d2[1], ix_mul_shift<K>(qi, ar));
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        fx<K + 1> u, v;
-#pragma unroll
-        for (int w = 0; w < K + 1; w++) {
-          u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
-          v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
-        }
-        dr = ix_add<K + 1>(dr, u);
-        di = ix_add<K + 1>(di, v);
-      }
-      __syncthreads();
-      if (lane == 0) {
-        sWarpD[2 * warp] = dr;
-        sWarpD[2 * warp + 1] = di;
-      }
-      __syncthreads();
+      allok = cluster_sum<K + 1, 2>(d2, sWarpD, sCritD, sOk + 2 + (k & 1), okv, cl);
       if (tid == 0) {
-        for (int w = 1; w < MF_WARPS; w++) {
-          dr = ix_add<K + 1>(dr, sWarpD[2 * w]);
-          di = ix_add<K + 1>(di, sWarpD[2 * w + 1]);
-        }
-        sCritD[0] = dr;
-        sCritD[1] = di;
-      }
-      cl.sync();
-      if (tid == 0) {
-        fx<K + 1> tr, ti;
-        fx_zero<K + 1>(tr);
-        fx_zero<K + 1>(ti);
-        for (int r = 0; r < MF_C; r++) {
-          const fx<K + 1> *p = cl.map_shared_rank(sCritD, r);
-          tr = ix_add<K + 1>(tr, p[0]);
-          ti = ix_add<K + 1>(ti, p[1]);
-        }
-        sR[2 * a.maxown] = ix_narrow<K>(tr);
-        sR[2 * a.maxown + 1] = ix_narrow<K>(ti);
-        if (rank == 0 && a.Rm) {
-          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
-          rm[0] = sR[2 * a.maxown];
-          rm[1] = sR[2 * a.maxown + 1];
-        }
-        if (rank == 0) {
-          cx<L> rk;
-          fx_to_cascade<K + 1, L>(tr, -sj, rk.re);
-          fx_to_cascade<K + 1, L>(ti, -sj, rk.im);
-          c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
-        }
+        *sAll = allok;
+        sR[2 * a.maxown] = ix_narrow<K>(d2[0]);
+        sR[2 * a.maxown + 1] = ix_narrow<K>(d2[1]);
       }
       __syncthreads();
+      allok = *sAll;
+      if (!allok) break;
       {
         const fx<K> rr = sR[2 * a.maxown], ri = sR[2 * a.maxown + 1];
         for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
@@ -393,6 +421,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
             x = ix_sub<K + 1>(x, ix_mul_shift<K>(ri, qr));
           }
           aj[2 * i + part] = ix_narrow<K>(x);
+        }
+        if (tid == 0 && rank == 0) {
+          if (a.Rm) {
+            fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
+            rm[0] = rr;
+            rm[1] = ri;
+          }
+          cx<L> rk;
+          fx_to_cascade<K + 1, L>(d2[0], -sj, rk.re);
+          fx_to_cascade<K + 1, L>(d2[1], -sj, rk.im);
+          c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
         }
       }
       __syncthreads();
@@ -432,7 +471,13 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           sDot[(buf * a.maxown + c) * 2 + 1] = di;
         }
       }
+      if (tid == 0) sOk[buf] = (j1 % G == g) ? 1 : okv;  // lookahead already checked the wait
       cl.sync();
+      if (warp == 0) {
+        int okr = (lane < MF_C) ? cl.map_shared_rank(sOk, lane)[buf] : 1;
+        okr = __all_sync(0xffffffffu, okr);
+        if (lane == 0) *sAll = okr;
+      }
       for (int cc = tid; cc < nb; cc += MF_THREADS) {
         const int c = cb + cc;
         fx<K + 1> tr, ti;
@@ -445,12 +490,12 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
         sR[2 * c] = ix_narrow<K>(tr);
         sR[2 * c + 1] = ix_narrow<K>(ti);
-        if (rank == 0 && a.Rm) {
-          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)(g + G * c) * a.ldr + k) * W);
-          rm[0] = sR[2 * c];
-          rm[1] = sR[2 * c + 1];
-        }
         if (rank == 0) {
+          if (a.Rm) {
+            fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)(g + G * c) * a.ldr + k) * W);
+            rm[0] = sR[2 * c];
+            rm[1] = sR[2 * c + 1];
+          }
           cx<L> rk;
           fx_to_cascade<K + 1, L>(tr, -sS[c], rk.re);
           fx_to_cascade<K + 1, L>(ti, -sS[c], rk.im);
@@ -458,6 +503,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
       }
       __syncthreads();
+      if (!*sAll) break;
       for (int cc = warp; cc < nb; cc += MF_WARPS) {
         const int c = cb + cc;
         fx<K> *aj = col(g + G * c);
@@ -493,7 +539,7 @@ struct MiLayout {
     b += sizeof(fx<2 * K + 1>) * MF_WARPS;             // sWarpT
     b += sizeof(fx<K>) * 2 * (maxown + 1);             // sR
     b += sizeof(fx<K>) * 2 * (ms > 0 ? ms : 1);        // sQ
-    b += 16 + sizeof(fx<K>) + 64;                      // flags, Z, slack
+    b += 32 + 2 * sizeof(fx<K>) + 64;                  // flags, Z, t, slack
     bytes = (b + 255) & ~(size_t)255;
   }
 };

@@ -29,6 +29,11 @@ static void run(const char *op) {
   } else if (!strcmp(op, "sar")) {
     gn::fx<K> r = gn::ix_sar<K>(a, s);
     for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  } else if (!strcmp(op, "rsqrt")) {
+    gn::ux<K> t;
+    for (int i = 0; i < K; i++) t.w[i] = a.w[i];
+    gn::ux<K> y = gn::ix_rsqrt_frac<K>(t);
+    for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)y.w[i]);
   } else if (!strcmp(op, "bitlen")) {
     printf("%x ", gn::ix_bitlen<K>(a));
   }

@@ -95,3 +95,21 @@ def test_square_add_sub_sar_bitlen(harness, K):
             assert got[0] == want
         else:
             assert val(got) == want, kind
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_rsqrt_frac(harness, K):
+    """Y = 2^(64K-2)/sqrt(t) for t = tt/2^(64K) in [1/4, 1), to within a few units."""
+    import math
+    rng = np.random.default_rng(50 + K)
+    ts = [1 << (64 * K - 2), (1 << (64 * K)) - 1]
+    for _ in range(200):
+        v = int.from_bytes(rng.bytes(8 * K), "little")
+        ts.append((v >> 2) | (1 << (64 * K - 2)))
+    lines = [f"rsqrt {K} " + " ".join("%x" % x for x in limbs(t, K) + [0] * K) for t in ts]
+    S = 64 * K - 2
+    for t, got in zip(ts, run(harness, lines)):
+        Y = val(got, signed=False)
+        # exact: floor(2^S * sqrt(2^(64K) / t)) = isqrt(2^(2S + 64K) // t)
+        want = math.isqrt((1 << (2 * S + 64 * K)) // t)
+        assert abs(Y - want) <= 8, (K, t, Y - want)
