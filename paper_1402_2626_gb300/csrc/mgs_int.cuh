@@ -68,14 +68,16 @@ __device__ void rsqrt_cascade(const double (&s)[L], double (&y)[L]) {
   }
 }
 
-// Exact sum over the CTA, then over the cluster, of NV values of N limbs
-// held by every thread.  On return lanes 0..7 of warp 0 hold the cluster
-// totals in v.  sWarp: [MF_WARPS][NV] this CTA's scratch; sSlot: [NV] the slot
-// the cluster reads; *sOk / okv: this CTA's flag, ANDed over the cluster into
-// the return value (valid in warp 0).  Every thread of every CTA must call it.
+// Exact sum over the cluster of NV values of N limbs held by every thread:
+// each warp adds its lanes, writes the warp total to its slot in this CTA's
+// sSlot ([MF_WARPS][NV]), one cluster barrier, then warp 0 of every CTA adds
+// the MF_C x MF_WARPS slots.  On return all lanes of warp 0 hold the totals
+// in v.  *sOk = okv is this CTA's flag; the return value (valid in warp 0) is
+// the AND over the cluster.  Every thread of every CTA must call it, and two
+// calls with the same sSlot must be separated by another cluster barrier.
 template <int N, int NV>
-__device__ int cluster_sum(fx<N> (&v)[NV], fx<N> *sWarp, fx<N> *sSlot, int *sOk, int okv,
-                           cg::cluster_group &cl) {
+__device__ int cluster_sum(fx<N> (&v)[NV], fx<N> *sSlot, int *sOk, int okv, cg::cluster_group &cl) {
+  static_assert(MF_C * MF_WARPS == 64, "two slots per lane");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -86,42 +88,21 @@ __device__ int cluster_sum(fx<N> (&v)[NV], fx<N> *sWarp, fx<N> *sSlot, int *sOk,
       for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
       v[q] = ix_add<N>(v[q], u);
     }
-  __syncthreads();
   if (lane == 0)
 #pragma unroll
-    for (int q = 0; q < NV; q++) sWarp[warp * NV + q] = v[q];
-  __syncthreads();
-  if (warp == 0) {
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-      if (lane < MF_WARPS) v[q] = sWarp[lane * NV + q];
-      else fx_zero<N>(v[q]);
-#pragma unroll
-      for (int o = 4; o > 0; o >>= 1) {
-        fx<N> u;
-#pragma unroll
-        for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
-        v[q] = ix_add<N>(v[q], u);
-      }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < NV; q++) sSlot[q] = v[q];
-      *sOk = okv;
-    }
-  }
+    for (int q = 0; q < NV; q++) sSlot[warp * NV + q] = v[q];
+  if (threadIdx.x == 0) *sOk = okv;
   cl.sync();
   int all = 1;
   if (warp == 0) {
-    int okr = 1;
+    const int e0 = lane, e1 = lane + 32;
+    const fx<N> *p0 = cl.map_shared_rank(sSlot, e0 / MF_WARPS) + (e0 % MF_WARPS) * NV;
+    const fx<N> *p1 = cl.map_shared_rank(sSlot, e1 / MF_WARPS) + (e1 % MF_WARPS) * NV;
 #pragma unroll
-    for (int q = 0; q < NV; q++) {
-      if (lane < MF_C) v[q] = cl.map_shared_rank(sSlot, lane)[q];
-      else fx_zero<N>(v[q]);
-    }
-    if (lane < MF_C) okr = *cl.map_shared_rank(sOk, lane);
+    for (int q = 0; q < NV; q++) v[q] = ix_add<N>(p0[q], p1[q]);
+    int okr = (lane < MF_C) ? *cl.map_shared_rank(sOk, lane) : 1;
 #pragma unroll
-    for (int o = 4; o > 0; o >>= 1)
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
       for (int q = 0; q < NV; q++) {
         fx<N> u;
@@ -152,14 +133,13 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
 
   // shared memory
   int *sS = (int *)smem;                                   // [maxown] column exponents s_j
-  double *sN0 = (double *)(smem + 16 * ((a.maxown * 4 + 15) / 16));  // [maxown]
+  int *sTb = sS + a.maxown;                                // [maxown] rank-test bit lengths
+  double *sN0 = (double *)(smem + 16 * ((a.maxown * 8 + 15) / 16));  // [maxown]
   double *sN0p = sN0 + a.maxown;                           // [maxown]
   fx<K + 1> *sDot = (fx<K + 1> *)(sN0p + a.maxown);        // [2][maxown][2] bulk partials
-  fx<K + 1> *sCritD = sDot + 4 * a.maxown;                 // [2] critical dot partial
-  fx<2 * K + 1> *sCritT = (fx<2 * K + 1> *)(sCritD + 2);   // [1] critical norm partial
-  fx<K + 1> *sWarpD = (fx<K + 1> *)(sCritT + 1);           // [MF_WARPS][2]
-  fx<2 * K + 1> *sWarpT = (fx<2 * K + 1> *)(sWarpD + 2 * MF_WARPS);  // [MF_WARPS]
-  fx<K> *sR = (fx<K> *)(sWarpT + MF_WARPS);                // [maxown + 1][2] r_kj mantissas
+  fx<K + 1> *sCritD = sDot + 4 * a.maxown;                 // [MF_WARPS][2] lookahead dot slots
+  fx<2 * K + 1> *sCritT = (fx<2 * K + 1> *)(sCritD + 2 * MF_WARPS);  // [MF_WARPS] norm slots
+  fx<K> *sR = (fx<K> *)(sCritT + MF_WARPS);                // [maxown + 1][2] r_kj mantissas
   fx<K> *sQ = sR + 2 * (a.maxown + 1);                     // [ms][2] pivot slice
   // wait results read by the cluster: [0,1] bulk step by parity, [2,3]
   // lookahead step by parity, [4] the pivot's (always 1)
@@ -193,6 +173,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     sN0[c] = n0;
     const int sj = fx_exponent_of(n0 * 1.0000001 + 1e-300) - S;
     sS[c] = sj;
+    // rank test: ||a_j||^2 = T 2^(2 s_j) must exceed (||a_j^0|| 2^(8-50L))^2, taken
+    // on bit lengths: reject when bitlen(T) <= 2 (floor(log2 ||a_j^0||) + 8 - 50L - s_j) + 1
+    sTb[c] = 2 * (fx_exponent_of(n0) - 1 + 8 - 50 * L - sj) + 1;
     if (rank == 0) {
       a.nrm0[g + G * c] = n0;
       a.nrm0[ncols + g + G * c] = (double)sj;
@@ -230,18 +213,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       const int i = i0 + (e >> 1), part = e & 1;
       t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * i + part]));
     }
-    cluster_sum<2 * K + 1, 1>(t, sWarpT, sCritT, sOk + 4, 1, cl);
+    cluster_sum<2 * K + 1, 1>(t, sCritT, sOk + 4, 1, cl);
     ux<K> Y;
     int bl = 0, b = 0;
     if (tid == 0) {
       const fx<2 * K + 1> T = t[0];
       bl = ix_bitlen<2 * K + 1>(T);
       b = (bl + 1) >> 1;  // sqrt(T) < 2^b
-      // rank test on ||a_j||^2 against (||a_j^0|| 2^(8-50L))^2
-      double tl[1];
-      fx_to_cascade<2 * K + 1, 1>(T, -2 * sj, tl);
-      const double th = ldexp(sN0[c], 8 - 50 * L);
-      int accept = (bl > 0) && (j == ncols - 1 || tl[0] > th * th);
+      int accept = (bl > 0) && (j == ncols - 1 || bl > sTb[c]);
       if (!accept && j < ncols - 1) atomicCAS(a.status, GN_OK, GN_ESINGULAR);
       // t = T / 2^(2b) in [1/4, 1) as K limbs of fraction
       ux<K> tt;
@@ -398,7 +377,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           d2[1] = ix_sub<K + 1>(d2[1], ix_mul_shift<K>(qi, ar));
         }
       }
-      allok = cluster_sum<K + 1, 2>(d2, sWarpD, sCritD, sOk + 2 + (k & 1), okv, cl);
+      allok = cluster_sum<K + 1, 2>(d2, sCritD, sOk + 2 + (k & 1), okv, cl);
       if (tid == 0) {
         *sAll = allok;
         sR[2 * a.maxown] = ix_narrow<K>(d2[0]);
@@ -422,20 +401,21 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           }
           aj[2 * i + part] = ix_narrow<K>(x);
         }
-        if (tid == 0 && rank == 0) {
-          if (a.Rm) {
-            fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
-            rm[0] = rr;
-            rm[1] = ri;
-          }
-          cx<L> rk;
-          fx_to_cascade<K + 1, L>(d2[0], -sj, rk.re);
-          fx_to_cascade<K + 1, L>(d2[1], -sj, rk.im);
-          c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
-        }
       }
       __syncthreads();
       pivot(j1, c);
+      if (tid == 0 && rank == 0) {  // r_kj of the lookahead column, after the publication
+        const fx<K> rr = sR[2 * a.maxown], ri = sR[2 * a.maxown + 1];
+        if (a.Rm) {
+          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
+          rm[0] = rr;
+          rm[1] = ri;
+        }
+        cx<L> rk;
+        fx_to_cascade<K, L>(rr, -sj, rk.re);
+        fx_to_cascade<K, L>(ri, -sj, rk.im);
+        c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
+      }
       cb = c + 1;
     }
     const int nb = no - cb;
@@ -531,12 +511,10 @@ struct MiLayout {
   size_t bytes;
   __host__ __device__ MiLayout(int maxown, int ms) {
     constexpr int K = L;
-    size_t b = 16 * ((maxown * 4 + 15) / 16);
+    size_t b = 16 * ((maxown * 8 + 15) / 16);
     b += 16 * maxown;                                  // sN0, sN0p
-    b += sizeof(fx<K + 1>) * (4 * maxown + 2);         // sDot, sCritD
-    b += sizeof(fx<2 * K + 1>);                        // sCritT
-    b += sizeof(fx<K + 1>) * 2 * MF_WARPS;             // sWarpD
-    b += sizeof(fx<2 * K + 1>) * MF_WARPS;             // sWarpT
+    b += sizeof(fx<K + 1>) * (4 * maxown + 2 * MF_WARPS);  // sDot, sCritD
+    b += sizeof(fx<2 * K + 1>) * MF_WARPS;             // sCritT
     b += sizeof(fx<K>) * 2 * (maxown + 1);             // sR
     b += sizeof(fx<K>) * 2 * (ms > 0 ? ms : 1);        // sQ
     b += 32 + 2 * sizeof(fx<K>) + 64;                  // flags, Z, t, slack
