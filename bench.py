@@ -37,10 +37,17 @@ METRIC = "complex DD/QD monomial eval+diff/s; Newton steps/s; % of FP64 peak vs 
 UNIT = "Newton steps/s"
 WORKLOAD = "gn256"
 L2_BYTES = 129 * 2 ** 20
-# FP64 issue rate used as the ALU roofline: 2 FP64 lanes per clock per SM
-# (the nominal 1.25 TFLOP/s FMA rate of GB300) x 152 SMs x 2070 MHz.
+# FP64 issue rate: 2 FP64 lanes per clock per SM (the nominal 1.25 TFLOP/s
+# FMA rate of GB300) x 152 SMs x 2070 MHz, in G lane-instructions/s.
 FP64_PEAK_GINSTR = 2 * 152 * 2.070
+# 32-bit integer multiply-add issue rate: 64 IMAD lanes per clock per SM (half
+# the 128 FP32 lanes; 19 T lane-ops/s measured on this part) x 152 SMs x
+# 2070 MHz, in G lane-instructions/s.
+IMAD_PEAK_GINSTR = 64 * 152 * 2.070
 PRECS = {"d": 1, "dd": 2, "qd": 4}
+# kernels one Gauss-Newton step launches (integer arithmetic): k_powers,
+# k_monomials, k_sum_jacobian, k_sum_f, k_mgs_int, k_backsub_int, k_update
+LAUNCHES_PER_STEP = 7
 
 # FP64 instructions (DADD, DMUL, DFMA each one) per complex operation of the
 # device arithmetic in csrc/mw.cuh, counted from the source.
@@ -72,6 +79,42 @@ def algorithmic_fp64(system, L):
     mgs_ops = pairs * 2 * (c["mul"] + c["add"]) + (n + 1) * m * (c["abs2"] + c["add"] + c["mul_real"])
     back_ops = n * (n - 1) // 2 * (c["mul"] + c["add"]) + n * c["mul_real"]
     return eval_ops, mgs_ops + back_ops
+
+
+def algorithmic_imad_mgs(m, ncols, L):
+    """32-bit partial products (IMAD lane-instructions) of the MGS factorisation
+    (Section 3) of an m x ncols complex matrix with L-limb integer mantissas:
+    every column's norm (2 real squares per entry) and normalisation (2 real
+    products per entry), and per column pair one dot and one axpy (4 real
+    products per entry each); a real product of two L-limb mantissas is
+    L^2 64 x 64-bit products of 4 partial products each."""
+    pairs = ncols * (ncols - 1) // 2
+    real_products = ncols * 4 * m + pairs * 8 * m
+    return real_products * 4 * L * L
+
+
+def rank_system(rank: int):
+    """The independent system rank ``rank`` solves (weak scaling: one seeded
+    system per rank, no exchange on the data path)."""
+    from paper_1402_2626_gb300 import inputs
+
+    return inputs.workload(WORKLOAD, rank)
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest ``value`` over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, t_max: float) -> float:
+    """Whole-job Newton steps/s: every rank takes ``steps`` steps of its own system."""
+    return world * steps / t_max
 
 
 class ClockSampler:
@@ -224,7 +267,7 @@ def main():
     if dist:
         dist.barrier()
     L = PRECS[args.prec]
-    system = inputs.workload(WORKLOAD, rank)
+    system = rank_system(rank)
     S = gn.System(system)
     x0 = torch.tensor(system.point("x0", L), device=dev)
     x = x0.clone()
@@ -260,13 +303,8 @@ def main():
     clk = clocks.stop() if rank == 0 else {}
     step_ms = [a.elapsed_time(b) for a, b in evs]
     t_local = sum(step_ms) / 1e3
-    t_max = t_local
-    if dist:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * args.steps / t_max
-    launches_per_step = 4 + 1 + (system.n + 1) + system.n + 2
+    t_max = max_over_ranks(t_local, dist, dev)
+    value = job_throughput(world, args.steps, t_max)
 
     # ---- end to end through host buffers: H2D of x, gn_newton, D2H of x
     hx0 = torch.tensor(system.point("x0", L)).pin_memory()
@@ -281,12 +319,8 @@ def main():
         hx.copy_(x, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t))
-    e2e_local = sum(e2e_ms) / 1e3
-    if dist:
-        tt = torch.tensor([e2e_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_local = float(tt.item())
-    e2e = {"value": world * args.steps / e2e_local, "unit": UNIT,
+    e2e_local = max_over_ranks(sum(e2e_ms) / 1e3, dist, dev)
+    e2e = {"value": job_throughput(world, args.steps, e2e_local), "unit": UNIT,
            "h2d_bytes_per_step": int(hx0.numel() * 8), "d2h_bytes_per_step": int(hx.numel() * 8 + 8 * 2 * 64 * 3)}
 
     extras = {}
@@ -304,7 +338,7 @@ def main():
                        "k": 16, "dmax": 5, "T": system.T, "precision": args.prec,
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "l2": "flushed between timed steps (256 MiB write)"},
-            "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e, "gpu_launches": LAUNCHES_PER_STEP * args.steps,
             "clocks": clk, "roofline": roofline, **extras,
         }
         if not args.no_cpu:
@@ -317,15 +351,34 @@ def main():
 
 
 def breakdown(S, system, dev, flush, args):
-    """Per-precision eval+diff and least-squares times (device events, L2 flushed)."""
+    """Per-precision eval+diff (integer and FP64 arithmetic), least-squares and
+    step times, and the roofline of the factorisation kernel (device events,
+    L2 flushed before every timed call)."""
     import torch
-
-    from paper_1402_2626_gb300 import gn
 
     reps = max(5, min(args.steps, 20))
     stream = torch.cuda.current_stream(dev)
     out = {"eval_diff": {}, "lstsq_ms": {}, "newton_step_ms": {}}
     roof = None
+
+    def timed(fn, prep=None):
+        for _ in range(2):
+            if prep:
+                prep()
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            if prep:
+                prep()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
     for prec, L in PRECS.items():
         x = torch.tensor(system.point("x0", L), device=dev)
         f = torch.empty((system.N, 2, L), dtype=torch.float64, device=dev)
@@ -333,47 +386,46 @@ def breakdown(S, system, dev, flush, args):
         Ab = torch.empty((system.n + 1, system.N, 2, L), dtype=torch.float64, device=dev)
         R = torch.empty((system.n + 1, system.n + 1, 2, L), dtype=torch.float64, device=dev)
         dx = torch.empty((system.n, 2, L), dtype=torch.float64, device=dev)
-
-        def timed(fn, prep=None):
-            for _ in range(2):
-                if prep:
-                    prep()
-                fn()
-            ms = []
-            for _ in range(reps):
-                flush.zero_()
-                if prep:
-                    prep()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                fn()
-                b.record(stream)
-                torch.cuda.synchronize()
-                ms.append(a.elapsed_time(b))
-            return statistics.median(ms)
-
-        t_eval = timed(lambda: S.eval(prec, x, f, J))
+        status = torch.zeros((1,), dtype=torch.int32, device=dev)
+        ev_ops, _ = algorithmic_fp64(system, L)
+        ev = {}
+        for arith in ("fp64", "int"):
+            S.set_arith(arith)
+            t = timed(lambda: S.eval(prec, x, f, J))
+            ev[arith] = {"ms": t, "monomials_per_s": system.T / (t / 1e3)}
+        S.set_arith("auto")
+        g = ev_ops / (ev["fp64"]["ms"] / 1e3) / 1e9
+        ev["fp64"]["fp64_ginstr_per_s"] = g
+        ev["fp64"]["frac_of_fp64_peak"] = g / FP64_PEAK_GINSTR
+        ev["int"]["speedup_vs_fp64"] = ev["fp64"]["ms"] / ev["int"]["ms"]
+        out["eval_diff"][prec] = ev
+        S.eval(prec, x, f, J)
         Ab0 = torch.cat([J, -f[None]], 0).contiguous()
 
         def prep_ab():
             Ab.copy_(Ab0)
 
-        t_ls = timed(lambda: S.lstsq(prec, Ab, R, dx), prep_ab)
+        out["lstsq_ms"][prec] = timed(lambda: S.lstsq(prec, Ab, R, dx), prep_ab)
         x0 = torch.tensor(system.point("x0", L), device=dev)
-        t_step = timed(lambda: S.newton(prec, x, 1), lambda: x.copy_(x0))
-        ev_ops, ls_ops = algorithmic_fp64(system, L)
-        out["eval_diff"][prec] = {"monomials_per_s": system.T / (t_eval / 1e3), "ms": t_eval,
-                                  "fp64_ginstr_per_s": ev_ops / (t_eval / 1e3) / 1e9}
-        out["lstsq_ms"][prec] = t_ls
-        out["newton_step_ms"][prec] = t_step
+        out["newton_step_ms"][prec] = timed(lambda: S.newton(prec, x, 1), lambda: x.copy_(x0))
         if prec == args.prec:
-            achieved = ls_ops / (t_ls / 1e3) / 1e9
-            roof = {"kernel": "MGS least squares (k_mgs_pivot, k_mgs_update, k_backsub)",
-                    "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GINSTR,
-                    "unit": "G FP64 instr/s", "frac": achieved / FP64_PEAK_GINSTR,
-                    "peak_source": "derived: 2 FP64 lanes/clk/SM x 152 SMs x 2.07 GHz",
-                    "traffic": None,
-                    "algorithmic_fp64_instr": ls_ops}
+            # the dominant kernel of the step: k_mgs_int, through gn_mgs (its
+            # time includes the zeroing of R and the conversion of Q back to
+            # cascades, together under 1% of the factorisation)
+            t_mgs = timed(lambda: S.mgs(prec, Ab, R, status), prep_ab)
+            assert int(status.item()) == 0
+            work = algorithmic_imad_mgs(system.N, system.n + 1, L)
+            achieved = work / (t_mgs / 1e3) / 1e9
+            roof = {"kernel": f"k_mgs_int<{L}> (MGS on [J, -f], {system.N} x {system.n + 1})",
+                    "bound": "alu", "achieved": achieved, "peak": IMAD_PEAK_GINSTR,
+                    "unit": "G IMAD/s", "frac": achieved / IMAD_PEAK_GINSTR,
+                    "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2.07 GHz",
+                    # ncu, one DD launch inside the Newton step (k_mgs_int_dd_gn256.md)
+                    "traffic": 2.50e6 if L == 2 else None,
+                    "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch",
+                    "algorithmic_imad": work, "launch_ms": t_mgs,
+                    "us_per_column": 1e3 * t_mgs / (system.n + 1),
+                    "note": "latency-bound: one dependent pivot step per column"}
     return out, roof
 
 

@@ -93,6 +93,28 @@ gn_status gn_system_create(gn_system **out, int32_t N, int32_t n, int64_t T,
 /* Free a system and all workspaces it holds (synchronizes the device). */
 gn_status gn_system_destroy(gn_system *s);
 
+/*
+ * Arithmetic of evaluation (Section 2) and least squares (Section 3) at every
+ * precision.  Inputs and outputs keep the cascade layout either way.
+ *   GN_ARITH_INT : integer mantissas with one binary exponent per complex
+ *                  value (evaluation) or per column (MGS and back
+ *                  substitution); 62, 126 and 254 mantissa bits for L = 1, 2, 4,
+ *                  so at least the precision of the cascades; products and
+ *                  sums run on the integer pipe.
+ *   GN_ARITH_FP64: the cascades themselves, combined by error-free
+ *                  transformations of doubles (the paper's double double and
+ *                  quad double arithmetic) on the FP64 pipe, with MGS as one
+ *                  launch per pivot.
+ *   GN_ARITH_AUTO (default): the faster of the two per step on this GPU:
+ *                  FP64 evaluation in double precision, integer evaluation in
+ *                  DD and QD, integer least squares at every precision.
+ * All three meet the accuracy stated for gn_eval, gn_lstsq and gn_newton.
+ * Changing it discards the Newton step graphs the system has captured.
+ * Returns GN_EINVAL for a null system or an unknown value.
+ */
+typedef enum { GN_ARITH_AUTO = 0, GN_ARITH_INT = 1, GN_ARITH_FP64 = 2 } gn_arith;
+gn_status gn_system_set_arith(gn_system *s, gn_arith arith);
+
 /* Basic facts about a loaded system (any pointer may be NULL). */
 gn_status gn_system_info(const gn_system *s, int32_t *N, int32_t *n, int64_t *T,
                          int64_t *nnz, int32_t *max_support);
@@ -116,15 +138,28 @@ gn_status gn_eval(gn_system *s, gn_prec prec, const double *d_x, double *d_f,
  *   d_Ab : m x (n+1) complex, column-major with leading dimension ldAb >= m;
  *          columns 0..n-1 are A, column n is b.  Overwritten: columns 0..n-1
  *          by Q, column n by b - Q y (its norm is z of eq. 2).
- *   d_R  : (n+1) x (n+1) complex, column-major, ld n+1, output (may be NULL to
- *          use library workspace); R[k][k] real positive, R[0:n, n] = y,
- *          R[n][n] = z, zeros below the diagonal.
+ *   d_R  : (n+1) x (n+1) complex, column-major, ld n+1, output (not NULL);
+ *          R[k][k] real positive, R[0:n, n] = y, R[n][n] = z, zeros below
+ *          the diagonal.
  *   d_dx : [n] complex, output: the least-squares solution of A dx = b.
  * Returns GN_ESINGULAR (after synchronizing) when a pivot r_kk, k < n, is at
- * most 2^(8-50L) times the original norm of column k.
+ * most 2^(8-50L) times the original norm of column k (under GN_ARITH_INT the
+ * test compares bit lengths, so the threshold holds within a factor of 2).
  */
 gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
                    int64_t ldAb, double *d_R, double *d_dx, void *cuda_stream);
+
+/*
+ * The factorisation of gn_lstsq alone: modified Gram-Schmidt on [A b]
+ * (Section 3, eq. 2) without the back substitution, fully stream-ordered.
+ *   d_Ab, ldAb, d_R : as for gn_lstsq (Q and b - Q y overwrite d_Ab; R into d_R).
+ *   d_status : device int32 the caller owns; when the kernels finish it holds
+ *              GN_OK, GN_ESINGULAR (the rank test of gn_lstsq) or GN_ETIMEOUT.
+ * Requires n <= the system's number of variables (it uses the system's
+ * workspace).  Does not synchronize: check *d_status after the stream does.
+ */
+gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
+                 double *d_R, int32_t *d_status, void *cuda_stream);
 
 /*
  * Take up to `steps` Gauss-Newton steps (Section 4) in place on d_x:
@@ -152,6 +187,7 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  * library routine.  Its scratch is one static device array of
  * GN_NOALLOC_SCRATCH_BYTES inside the library, which every process that
  * loads the library holds on each GPU it uses until it exits.
+ *   It always evaluates with GN_ARITH_FP64 arithmetic.
  *   Arguments, layouts and outputs are those of gn_eval; d_x, d_f and d_J
  *   remain caller memory and the system must already be loaded (loading it
  *   allocates).

@@ -1,0 +1,251 @@
+// eval_int.cu — evaluation and differentiation (Section 2) with
+// integer-mantissa complex arithmetic (cf.cuh): the same schedule as eval.cu
+// (power table, common factor folded into the forward products, one running
+// backward product, exponent factors, owner-computed term sums), with every
+// product and sum on the integer pipe instead of FP64 error-free
+// transformations.  Term sums align the contributions to the largest
+// exponent among them and add the mantissas exactly.
+#include "cf.cuh"
+#include "internal.h"
+#include "mw.cuh"
+
+namespace gn {
+
+constexpr int KMAXI = 64;
+
+// words (8 bytes) per staged complex value: re mantissa, im mantissa, exponent
+template <int L>
+struct CfStore {
+  static constexpr int WORDS = 2 * L + 1;
+};
+
+template <int K>
+__device__ __forceinline__ void cf_st(double *p, const cf<K> &z) {
+  uint64_t *q = (uint64_t *)p;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    q[w] = z.re.w[w];
+    q[K + w] = z.im.w[w];
+  }
+  q[2 * K] = (uint64_t)(int64_t)z.e;
+}
+
+template <int K>
+__device__ __forceinline__ cf<K> cf_ld(const double *p) {
+  const uint64_t *q = (const uint64_t *)p;
+  cf<K> z;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    z.re.w[w] = __ldg(q + w);
+    z.im.w[w] = __ldg(q + K + w);
+  }
+  z.e = (int)(int64_t)__ldg(q + 2 * K);
+  return z;
+}
+
+template <int L>
+__global__ void k_powers_cf(const double *__restrict__ x, int32_t n, int32_t pmax,
+                            double *__restrict__ pow, const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n || *status != GN_OK) return;
+  double re[L], im[L];
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    re[l] = x[(int64_t)v * 2 * L + l];
+    im[l] = x[(int64_t)v * 2 * L + L + l];
+  }
+  const cf<L> xv = cf_from_cascade<L, L>(re, im);
+  cf<L> p = xv;
+  cf_st<L>(pow + (int64_t)v * WS, p);
+  for (int q = 1; q < pmax; q++) {
+    p = cf_mul<L>(p, xv);
+    cf_st<L>(pow + ((int64_t)q * n + v) * WS, p);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(128) k_monomials_cf(
+    const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
+    const double *__restrict__ coef, int64_t T, const double *__restrict__ pow, int32_t n,
+    double *__restrict__ stage_val, double *__restrict__ stage_d,
+    const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T || *status != GN_OK) return;
+  const int o0 = __ldg(mono_off + t);
+  const int k = __ldg(mono_off + t + 1) - o0;
+  double cre[L], cim[L];
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    cre[l] = __ldg(coef + (int64_t)(2 * l + 0) * T + t);
+    cim[l] = __ldg(coef + (int64_t)(2 * l + 1) * T + t);
+  }
+  cf<L> a = cf_from_cascade<L, L>(cre, cim);
+  for (int s = 0; s < k; s++) {
+    uint32_t w = __ldg(occ + o0 + s);
+    int d = (int)(w & 255u);
+    if (d >= 2) a = cf_mul<L>(a, cf_ld<L>(pow + ((int64_t)(d - 2) * n + (w >> 8)) * WS));
+  }
+  if (k == 0) {
+    cf_st<L>(stage_val + t * WS, a);
+    return;
+  }
+  cf<L> F[KMAXI];
+  F[0] = a;
+  for (int s = 1; s < k; s++) {
+    int v = (int)(__ldg(occ + o0 + s - 1) >> 8);
+    F[s] = cf_mul<L>(F[s - 1], cf_ld<L>(pow + (int64_t)v * WS));
+  }
+  uint32_t wl = __ldg(occ + o0 + k - 1);
+  cf<L> B = cf_ld<L>(pow + (int64_t)(wl >> 8) * WS);
+  cf_st<L>(stage_val + t * WS, cf_mul<L>(F[k - 1], B));
+  cf_st<L>(stage_d + (int64_t)(o0 + k - 1) * WS, cf_scale_int<L>(F[k - 1], wl & 255u));
+  for (int s = k - 2; s >= 0; s--) {
+    uint32_t w = __ldg(occ + o0 + s);
+    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_int<L>(cf_mul<L>(F[s], B), w & 255u));
+    if (s > 0) B = cf_mul<L>(B, cf_ld<L>(pow + (int64_t)(w >> 8) * WS));
+  }
+}
+
+// Exact-alignment term sums (Section 2.3).  The common exponent E is the
+// largest exponent among the terms plus the bit length of their count, so
+// that the sum cannot overflow; each K-limb mantissa goes to the top K limbs
+// of a (K+1)-limb accumulator (64 guard bits) and shifts right by E - e.  The
+// accumulator then holds the sum in units of 2^(E - 64), and the only error
+// is the truncation of each term below that unit.
+template <int K>
+__device__ __forceinline__ void cf_accumulate(fx<K + 1> &re, fx<K + 1> &im, const cf<K> &z, int E) {
+  if (z.e == CF_EZERO) return;
+  const int s = E - z.e;
+  if (s >= 64 * K + 62) return;  // entirely below the accumulator's unit
+  fx<K + 1> a, b;
+  a.w[0] = 0;
+  b.w[0] = 0;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    a.w[w + 1] = z.re.w[w];
+    b.w[w + 1] = z.im.w[w];
+  }
+  re = ix_add<K + 1>(re, ix_sar<K + 1>(a, s));
+  im = ix_add<K + 1>(im, ix_sar<K + 1>(b, s));
+}
+
+// exponent of the sums of c terms whose largest exponent is emax
+__device__ __forceinline__ int cf_sum_exponent(int emax, int c) {
+  return emax == CF_EZERO ? CF_EZERO : emax + (32 - __clz(c > 0 ? c : 1));
+}
+
+template <int L>
+__device__ __forceinline__ void cf_store_cascade(double *dst, const fx<L + 1> &re, const fx<L + 1> &im,
+                                                 int E, bool neg) {
+  double r[L], i[L];
+  if (E == CF_EZERO) {
+#pragma unroll
+    for (int l = 0; l < L; l++) r[l] = i[l] = 0.0;
+  } else {
+    fx_to_cascade<L + 1, L>(re, 64 - E, r);
+    fx_to_cascade<L + 1, L>(im, 64 - E, i);
+  }
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    dst[l] = neg ? -r[l] : r[l];
+    dst[L + l] = neg ? -i[l] : i[l];
+  }
+}
+
+template <int L>
+__global__ void k_sum_jacobian_cf(int64_t nz, const int32_t *__restrict__ jz_row,
+                                  const int32_t *__restrict__ jz_col,
+                                  const int32_t *__restrict__ jz_ptr,
+                                  const int32_t *__restrict__ jz_occ,
+                                  const double *__restrict__ stage_d, double *__restrict__ J,
+                                  int64_t ldJ, const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (z >= nz || *status != GN_OK) return;
+  const int p0 = __ldg(jz_ptr + z), p1 = __ldg(jz_ptr + z + 1);
+  int emax = CF_EZERO;
+  for (int p = p0; p < p1; p++) {
+    const int e = (int)(int64_t)__ldg((const uint64_t *)(stage_d + (int64_t)__ldg(jz_occ + p) * WS) + 2 * L);
+    emax = e > emax ? e : emax;
+  }
+  const int E = cf_sum_exponent(emax, p1 - p0);
+  fx<L + 1> re, im;
+  fx_zero<L + 1>(re);
+  fx_zero<L + 1>(im);
+  for (int p = p0; p < p1; p++) cf_accumulate<L>(re, im, cf_ld<L>(stage_d + (int64_t)__ldg(jz_occ + p) * WS), E);
+  cf_store_cascade<L>(J + ((int64_t)__ldg(jz_col + z) * ldJ + __ldg(jz_row + z)) * 2 * L, re, im, E, false);
+}
+
+template <int L>
+__global__ void k_sum_f_cf(int32_t N, const int32_t *__restrict__ poly_ptr,
+                           const double *__restrict__ stage_val, double *__restrict__ f, int neg,
+                           const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+  const int lane = threadIdx.x & 31;
+  if (i >= N || *status != GN_OK) return;
+  const int t0 = __ldg(poly_ptr + i), t1 = __ldg(poly_ptr + i + 1);
+  int emax = CF_EZERO;
+  for (int t = t0 + lane; t < t1; t += 32) {
+    const int e = (int)(int64_t)__ldg((const uint64_t *)(stage_val + (int64_t)t * WS) + 2 * L);
+    emax = e > emax ? e : emax;
+  }
+  const int E = cf_sum_exponent(__reduce_max_sync(0xffffffffu, emax), t1 - t0);
+  fx<L + 1> re, im;
+  fx_zero<L + 1>(re);
+  fx_zero<L + 1>(im);
+  for (int t = t0 + lane; t < t1; t += 32) cf_accumulate<L>(re, im, cf_ld<L>(stage_val + (int64_t)t * WS), E);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx<L + 1> u, v;
+#pragma unroll
+    for (int w = 0; w <= L; w++) {
+      u.w[w] = __shfl_xor_sync(0xffffffffu, re.w[w], o);
+      v.w[w] = __shfl_xor_sync(0xffffffffu, im.w[w], o);
+    }
+    re = ix_add<L + 1>(re, u);
+    im = ix_add<L + 1>(im, v);
+  }
+  if (lane == 0) cf_store_cascade<L>(f + (int64_t)i * 2 * L, re, im, E, neg != 0);
+}
+
+template <int L>
+static gn_status eval_int_impl(gn_system *s, Workspace *ws, const double *d_x, double *d_f, int neg_f,
+                               double *d_J, int64_t ldJ, cudaStream_t st) {
+  const int64_t W = 2 * L;
+  k_powers_cf<L><<<(s->n + 127) / 128, 128, 0, st>>>(d_x, s->n, s->pmax, ws->pow, ws->status);
+  if (s->T > 0)
+    k_monomials_cf<L><<<(unsigned)((s->T + 127) / 128), 128, 0, st>>>(
+        s->d_mono_off, s->d_occ, s->d_coef, s->T, ws->pow, s->n, ws->stage_val, ws->stage_d,
+        ws->status);
+  if (d_J) {
+    if (s->nz < (int64_t)s->N * s->n &&
+        cudaMemset2DAsync(d_J, sizeof(double) * W * ldJ, 0, sizeof(double) * W * s->N, s->n, st) !=
+            cudaSuccess)
+      return GN_ECUDA;
+    if (s->nz > 0)
+      k_sum_jacobian_cf<L><<<(unsigned)((s->nz + 127) / 128), 128, 0, st>>>(
+          s->nz, s->d_jz_row, s->d_jz_col, s->d_jz_ptr, s->d_jz_occ, ws->stage_d, d_J, ldJ,
+          ws->status);
+  }
+  if (d_f) k_sum_f_cf<L><<<(s->N + 3) / 4, 128, 0, st>>>(s->N, s->d_poly_ptr, ws->stage_val, d_f, neg_f, ws->status);
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
+gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
+                          double *d_J, int64_t ldJ, cudaStream_t st) {
+  if (s->kmax > KMAXI) return GN_EINVAL;
+  Workspace *ws;
+  gn_status e = workspace_get(s, L, &ws);
+  if (e) return e;
+  switch (L) {
+    case 1: return eval_int_impl<1>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
+    case 2: return eval_int_impl<2>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
+    case 4: return eval_int_impl<4>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
+  }
+  return GN_EINVAL;
+}
+
+}  // namespace gn

@@ -163,50 +163,63 @@ FX_HD void fx_neg(fx<NL> &a) {
   fx_add_to<NL>(a, z, 1);
 }
 
-// The value a * 2^-F as a cascade of L doubles (each the top 53 bits of the
-// remainder, truncated).
+// The value a * 2^-F as a cascade of L doubles: limb l is the double nearest
+// to what limbs 0..l-1 leave over (ties away from zero), so each limb after
+// the first is at most half an ulp of the one before and may have either
+// sign.
 template <int NL, int L>
 FX_HD void fx_to_cascade(fx<NL> a, int F, double (&out)[L]) {
-  const uint64_t sign = a.w[NL - 1] >> 63;
-  if (sign) fx_neg<NL>(a);
 #pragma unroll
   for (int l = 0; l < L; l++) {
-    // position p of the top set bit
+    const uint64_t sign = a.w[NL - 1] >> 63;
+    fx<NL> u = a;
+    if (sign) fx_neg<NL>(u);
+    // position p of the top set bit of |a|
     int p = -1;
 #pragma unroll
     for (int i = NL - 1; i >= 0; i--)
-      if (p < 0 && a.w[i]) p = 64 * i + 63 - fx_clz64(a.w[i]);
+      if (p < 0 && u.w[i]) p = 64 * i + 63 - fx_clz64(u.w[i]);
     if (p < 0) {
       out[l] = 0.0;
       continue;
     }
-    // the 53 bits [lo_bit, p] (fewer when p < 52)
     const int lo_bit = p - 52;
     uint64_t m;
-    if (lo_bit >= 0) {
+    if (lo_bit > 0) {
+      // the 53 bits [lo_bit, p], plus the bit below them rounded in
       const int li = lo_bit >> 6, off = lo_bit & 63;
-      uint64_t w0 = 0, w1 = 0;
+      const int rb = lo_bit - 1, ri = rb >> 6, ro = rb & 63;
+      uint64_t w0 = 0, w1 = 0, wr = 0;
 #pragma unroll
       for (int i = 0; i < NL; i++) {
-        if (i == li) w0 = a.w[i];
-        if (i == li + 1) w1 = a.w[i];
+        if (i == li) w0 = u.w[i];
+        if (i == li + 1) w1 = u.w[i];
+        if (i == ri) wr = u.w[i];
       }
-      m = (w0 >> off) | (off ? (w1 << (64 - off)) : 0);
-      m &= (1ull << 53) - 1;
-      // clear those bits
-      const uint64_t c0 = ((1ull << 53) - 1) << off;
-      const uint64_t c1 = off > 11 ? (((1ull << 53) - 1) >> (64 - off)) : 0;
+      m = ((w0 >> off) | (off ? (w1 << (64 - off)) : 0)) & ((1ull << 53) - 1);
+      m += (wr >> ro) & 1;  // m in [2^52, 2^53]
+      // u -= m 2^lo_bit (u may turn negative when rounded up)
+      fx<NL> v;
 #pragma unroll
       for (int i = 0; i < NL; i++) {
-        if (i == li) a.w[i] &= ~c0;
-        if (i == li + 1) a.w[i] &= ~c1;
+        uint64_t x = 0;
+        if (i == li) x = m << off;
+        if (i == li + 1 && off) x = m >> (64 - off);
+        v.w[i] = ~x;
       }
+      fx_add_to<NL>(u, v, 1);
     } else {
-      m = a.w[0] << (-lo_bit);
-      a.w[0] = 0;
+      m = u.w[0] << (-lo_bit);  // exact: nothing is left over
+      fx_zero<NL>(u);
     }
-    // value = m * 2^(lo_bit - F), m in [2^52, 2^53)
-    const int E = lo_bit - F;
+    // a = sign(a) * (|a| - m 2^lo_bit)
+    if (sign) fx_neg<NL>(u);
+    a = u;
+    int E = lo_bit - F;  // limb value m 2^E
+    if (m >> 53) {
+      m >>= 1;
+      E += 1;
+    }
     const int biased = E + 1075;
     if (biased <= 0 || biased >= 2047) {
       out[l] = 0.0;  // outside the normal range: not produced by the scales used here

@@ -59,9 +59,10 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   const size_t W = 2 * (size_t)L;
   const size_t n = s->n, N = s->N;
   gn_status e = GN_OK;
-  if (!e) e = dalloc(&w.pow, W * n * s->pmax);
-  if (!e) e = dalloc(&w.stage_val, W * s->T);
-  if (!e) e = dalloc(&w.stage_d, W * s->nnz);
+  const size_t SW = stage_words(L);
+  if (!e) e = dalloc(&w.pow, SW * n * s->pmax);
+  if (!e) e = dalloc(&w.stage_val, SW * s->T);
+  if (!e) e = dalloc(&w.stage_d, SW * s->nnz);
   if (!e) e = dalloc(&w.Ab, W * N * (n + 1));
   if (!e) e = dalloc(&w.R, W * (n + 1) * (n + 1));
   if (!e) e = dalloc(&w.dx, W * n);
@@ -243,7 +244,21 @@ gn_status gn_eval(gn_system *s, gn_prec prec, const double *d_x, double *d_f, do
   gn_status e = workspace_get(s, prec, &ws);
   if (e) return e;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  return launch_eval(s, prec, d_x, d_f, 0, d_J, ldJ, st);
+  return launch_eval_sel(s, prec, d_x, d_f, 0, d_J, ldJ, st);
+}
+
+gn_status gn_system_set_arith(gn_system *s, gn_arith arith) {
+  if (!s || (arith != GN_ARITH_AUTO && arith != GN_ARITH_INT && arith != GN_ARITH_FP64))
+    return GN_EINVAL;
+  if (s->arith == (int32_t)arith) return GN_OK;
+  s->arith = arith;
+  for (Workspace &w : s->ws)
+    if (w.step_exec) {
+      cudaGraphExecDestroy(w.step_exec);
+      w.step_exec = nullptr;
+      w.graph_x = nullptr;
+    }
+  return GN_OK;
 }
 
 gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
@@ -294,6 +309,25 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   return (gn_status)ws->h_status[0];
 }
 
+gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
+                 double *d_R, int32_t *d_status, void *cuda_stream) {
+  if (!s || !valid_prec(prec) || n < 1 || n > s->n || m < n || ldAb < m || !d_Ab || !d_R ||
+      !d_status)
+    return GN_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Workspace *ws;
+  gn_status e = workspace_get(s, prec, &ws);
+  if (e) return e;
+  if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
+  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
+                   ws->status, st, true);
+  if (e) return e;
+  if (cudaMemcpyAsync(d_status, ws->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
+      cudaSuccess)
+    return GN_ECUDA;
+  return GN_OK;
+}
+
 }  // extern "C"
 
 namespace gn {
@@ -303,7 +337,7 @@ namespace gn {
 static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cudaStream_t st) {
   const int64_t W = 2 * L;
   const int32_t N = s->N, n = s->n;
-  gn_status e = launch_eval(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
+  gn_status e = launch_eval_sel(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
   if (e) return e;
   e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, ws->dx,
                    ws->status, st, false);

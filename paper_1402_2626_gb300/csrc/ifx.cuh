@@ -193,17 +193,52 @@ FX_HD int ix_bitlen(const fx<N> &a) {
   return p;
 }
 
-// a >> s (arithmetic) for 0 <= s < 64 N
+// a >> s (arithmetic) for 0 <= s < 64 N.  The limb part of the shift is a
+// logarithmic barrel (one stage per bit of s / 64, each a select between
+// fixed limb positions), so a run-time s never indexes the register array.
 template <int N>
 FX_HD fx<N> ix_sar(const fx<N> &a, int s) {
   const int q = s >> 6, r = s & 63;
   const uint64_t sign = 0 - (a.w[N - 1] >> 63);
+  fx<N> t = a;
+#pragma unroll
+  for (int m = 1; m < N; m <<= 1) {
+    const bool on = (q & m) != 0;
+#pragma unroll
+    for (int i = 0; i < N; i++) {
+      const uint64_t v = (i + m < N) ? t.w[i + m] : sign;
+      t.w[i] = on ? v : t.w[i];
+    }
+  }
   fx<N> o;
 #pragma unroll
   for (int i = 0; i < N; i++) {
-    uint64_t lo = (i + q < N) ? a.w[i + q] : sign;
-    uint64_t hi = (i + q + 1 < N) ? a.w[i + q + 1] : sign;
-    o.w[i] = r ? ((lo >> r) | (hi << (64 - r))) : lo;
+    const uint64_t hi = (i + 1 < N) ? t.w[i + 1] : sign;
+    o.w[i] = r ? ((t.w[i] >> r) | (hi << (64 - r))) : t.w[i];
+  }
+  return o;
+}
+
+// a << s (bits shifted out of the top are lost) for 0 <= s < 64 N, with the
+// same barrel structure as ix_sar
+template <int N>
+FX_HD fx<N> ix_shl(const fx<N> &a, int s) {
+  const int q = s >> 6, r = s & 63;
+  fx<N> t = a;
+#pragma unroll
+  for (int m = 1; m < N; m <<= 1) {
+    const bool on = (q & m) != 0;
+#pragma unroll
+    for (int i = N - 1; i >= 0; i--) {
+      const uint64_t v = (i - m >= 0) ? t.w[i - m] : 0;
+      t.w[i] = on ? v : t.w[i];
+    }
+  }
+  fx<N> o;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    const uint64_t lo = (i - 1 >= 0) ? t.w[i - 1] : 0;
+    o.w[i] = r ? ((t.w[i] << r) | (lo >> (64 - r))) : t.w[i];
   }
   return o;
 }

@@ -37,6 +37,7 @@ struct gn_system {
   int32_t N = 0, n = 0;
   int64_t T = 0, nnz = 0;
   int32_t kmax = 0, dmax = 1, pmax = 1;
+  int32_t arith = GN_ARITH_AUTO;  // gn_arith of evaluation and least squares
   int32_t *d_poly_ptr = nullptr;  // [N+1] term ranges
   int32_t *d_mono_off = nullptr;  // [T+1] occurrence offsets
   uint32_t *d_occ = nullptr;      // [nnz] (var << 8) | exp
@@ -54,12 +55,31 @@ namespace gn {
 
 gn_status workspace_get(gn_system *s, int L, Workspace **out);
 
-// eval.cu
+// eval.cu: cascades of doubles with error-free transformations (FP64 pipe)
 gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
                       double *d_J, int64_t ldJ, cudaStream_t st);
+// eval_int.cu: integer mantissas with one exponent per complex value
+gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
+                          double *d_J, int64_t ldJ, cudaStream_t st);
+// whether the system's arithmetic evaluates (eval_int) or solves (lstsq) on
+// integer mantissas at precision L
+inline bool eval_int(const gn_system *s, int L) {
+  return s->arith == GN_ARITH_INT || (s->arith == GN_ARITH_AUTO && L > 1);
+}
+inline bool lstsq_int(const gn_system *s) { return s->arith != GN_ARITH_FP64; }
+// the evaluation the system's arithmetic selects
+inline gn_status launch_eval_sel(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
+                                 double *d_J, int64_t ldJ, cudaStream_t st) {
+  return eval_int(s, L) ? launch_eval_int(s, L, d_x, d_f, neg_f, d_J, ldJ, st)
+                        : launch_eval(s, L, d_x, d_f, neg_f, d_J, ldJ, st);
+}
+// words of one staged complex value: 2L limbs (cascades) or 2L mantissa limbs
+// and an exponent (integer evaluation)
+inline size_t stage_words(int L) { return 2 * (size_t)L + 1; }
 
 // lstsq.cu
-// want_q: convert Q back to L-limb cascades (gn_lstsq); the Newton step skips it
+// want_q: convert Q back to L-limb cascades (gn_lstsq); the Newton step skips it.
+// d_dx NULL: factorisation only (no back substitution).
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
                        double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q);
@@ -73,6 +93,8 @@ inline size_t lstsq_scratch_doubles(int32_t n, int L) { return (size_t)(n + 1) *
 
 // mgs.cu: MGS as one launch of thread-block clusters (0 clusters: unavailable)
 int mgs_flow_clusters(int L);
+// whether an m x ncols matrix fits the launch's shared-memory layout
+bool mgs_flow_fits(int L, int32_t m, int32_t ncols);
 gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncols, double *R,
                           int64_t ldr, double *rinv, uint32_t *flags, int32_t *status, double *Rm,
                           double *Zs, cudaStream_t st);

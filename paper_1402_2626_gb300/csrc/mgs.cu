@@ -464,6 +464,23 @@ static gn_status mi_to_cascade(double *A, int32_t m, int64_t lda, int32_t ncols,
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
+template <int L>
+static bool mf_fits(int32_t m, int32_t ncols) {
+  const int maxc = mf_max_clusters<L>(0, 0);
+  if (maxc <= 0) return false;
+  const int G = maxc < ncols ? maxc : ncols;
+  return MiLayout<L>((ncols + G - 1) / G, (m + MF_C - 1) / MF_C).bytes <= 227 * 1024;
+}
+
+bool mgs_flow_fits(int L, int32_t m, int32_t ncols) {
+  switch (L) {
+    case 1: return mf_fits<1>(m, ncols);
+    case 2: return mf_fits<2>(m, ncols);
+    case 4: return mf_fits<4>(m, ncols);
+  }
+  return false;
+}
+
 int mgs_flow_clusters(int L) {
   switch (L) {
     case 1: return mf_max_clusters<1>(0, 0);
@@ -477,18 +494,30 @@ template <int L>
 static gn_status bs_launch(const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                            const double *rinv, double *dx, int32_t *status, cudaStream_t st) {
   const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
-  const size_t bytes = (sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 64;
-  if (bytes > 48 * 1024 &&
-      cudaFuncSetAttribute(k_backsub_int<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-          cudaSuccess)
-    return GN_ECUDA;
-  k_backsub_int<L><<<1, BS_THREADS, bytes, st>>>(Rm, ldr, n, Zs, sexp, dx, status);
+  const size_t bytes = bs_smem_bytes<L>(n);
+  // one row per thread up to 512 unknowns, two up to 1024; whole warps
+  const int rows = n <= BS_MAX_THREADS ? 1 : 2;
+  const int per = (n + rows - 1) / rows;
+  const int threads = 32 * ((per + 31) / 32);
+  if (rows == 1) {
+    if (bytes > 48 * 1024 && cudaFuncSetAttribute(k_backsub_int<L, 1>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)bytes) != cudaSuccess)
+      return GN_ECUDA;
+    k_backsub_int<L, 1><<<1, threads, bytes, st>>>(Rm, ldr, n, Zs, sexp, dx, status);
+  } else {
+    if (bytes > 48 * 1024 && cudaFuncSetAttribute(k_backsub_int<L, 2>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)bytes) != cudaSuccess)
+      return GN_ECUDA;
+    k_backsub_int<L, 2><<<1, threads, bytes, st>>>(Rm, ldr, n, Zs, sexp, dx, status);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                              const double *rinv, double *dx, int32_t *status, cudaStream_t st) {
-  if (n > BS_THREADS * BS_ROWS) return GN_EINVAL;
+  if (n < 1 || n > 2 * BS_MAX_THREADS) return GN_EINVAL;
   switch (L) {
     case 1: return bs_launch<1>(Rm, ldr, n, Zs, rinv, dx, status, st);
     case 2: return bs_launch<2>(Rm, ldr, n, Zs, rinv, dx, status, st);

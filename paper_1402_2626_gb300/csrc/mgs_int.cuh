@@ -231,12 +231,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           sh = ix_sar<2 * K + 1>(T, d);
         } else {
           // left shift by -d (T < 2^(2b) < 2^(64K))
-          const int q = (-d) >> 6, r = (-d) & 63;
-#pragma unroll
-          for (int w = 2 * K; w >= 0; w--) {
-            uint64_t lo = (w - q >= 0) ? T.w[w - q] : 0, lo2 = (w - q - 1 >= 0) ? T.w[w - q - 1] : 0;
-            sh.w[w] = r ? ((lo << r) | (lo2 >> (64 - r))) : lo;
-          }
+          sh = ix_shl<2 * K + 1>(T, -d);
         }
 #pragma unroll
         for (int w = 0; w < K; w++) tt.w[w] = sh.w[w];
@@ -547,35 +542,154 @@ __global__ void k_mgs_int_to_cascade(double *A, int32_t m, int64_t lda, int32_t 
 }
 
 // Back substitution R[0:n,0:n] x = y on the mantissas the MGS kernel left
-// (Section 3, eq. 5 read as x_l = (y_l - sum_{j>l} r_lj x_j) / r_ll).
-// y is held in fixed point at the scale of the last column (K+2 limbs: two
-// limbs of headroom for intermediate growth), each x_l in block floating
-// point (K-limb mantissa per part, one exponent).  One thread per row;
-// level l: the owner of row l forms x_l = y_l / r_ll, then every row i < l
-// subtracts r_il x_l.  All integer.
-constexpr int BS_THREADS = 256;
-constexpr int BS_ROWS = 4;  // rows per thread: n <= 1024
+// (Section 3, eq. 5 read as x_l = (y_l - sum_{j>l} r_lj x_j) / r_ll), column
+// oriented: at level l every row i < l subtracts r_il x_l.  y is held in
+// fixed point at the scale of the last column (K+2 limbs: two limbs of
+// headroom for intermediate growth), each x_l in block floating point (K-limb
+// mantissa per part, one exponent).  One CTA; row i belongs to thread
+// i mod T.  The owner of row l-1 forms x_{l-1} as soon as its own update with
+// x_l is done, so a level costs one barrier; the r_il of a later level are
+// loaded while the current one runs, and the reciprocals 1/r_ll and the
+// column exponents sit in shared memory.  All integer.
+constexpr int BS_MAX_THREADS = 512;
 
-template <int L>
-__global__ void __launch_bounds__(BS_THREADS) k_backsub_int(const double *__restrict__ Rm, int64_t ldr,
-                                                            int32_t n, const double *__restrict__ Zs,
-                                                            const double *__restrict__ sexp,
-                                                            double *__restrict__ dx,
-                                                            int32_t *__restrict__ status) {
-  constexpr int K = L, W = 2 * L, KY = K + 2;
-  __shared__ fx<K> sX[2];
-  __shared__ int sT;
-  __shared__ int sFail;
-  extern __shared__ __align__(16) unsigned char bsm[];
-  fx<K> *sXall = (fx<K> *)bsm;                  // [n][2] mantissas of x
-  int *sTall = (int *)(sXall + 2 * (n > 0 ? n : 1));  // [n] exponents of x
-  if (*status != GN_OK) return;
-  const int tid = threadIdx.x;
-  const int sig = (int)sexp[n];  // scale of y (the last column)
-  fx<KY> Y[BS_ROWS][2];
+// x = y 2^sig * Z 2^e as a K-limb mantissa per part and the exponent t
+template <int K, int KY>
+__device__ __forceinline__ void bs_solve(const fx<KY> &yr, const fx<KY> &yi, const fx<K> &Z, int e,
+                                         int sig, fx<K> &Xr, fx<K> &Xi, int &t) {
+  uint64_t nz;
+  const ux<K> uz = ix_abs<K>(Z, nz);
+  fx<KY + K> P[2];
+  int B = 0;
 #pragma unroll
-  for (int p = 0; p < BS_ROWS; p++) {
-    const int i = tid + BS_THREADS * p;
+  for (int part = 0; part < 2; part++) {
+    uint64_t ny;
+    const ux<KY> uy = ix_abs<KY>(part ? yi : yr, ny);
+    // |y| |Z| as KY + K limbs
+#pragma unroll
+    for (int w = 0; w < KY + K; w++) P[part].w[w] = 0;
+#pragma unroll
+    for (int a = 0; a < KY; a++) {
+      u128_t carry = 0;
+#pragma unroll
+      for (int b = 0; b < K; b++) {
+        u128_t tt = (u128_t)uy.w[a] * uz.w[b] + P[part].w[a + b] + carry;
+        P[part].w[a + b] = (uint64_t)tt;
+        carry = tt >> 64;
+      }
+      P[part].w[a + K] = (uint64_t)carry;
+    }
+    const int bl = ix_bitlen<KY + K>(P[part]);
+    B = bl > B ? bl : B;
+    ix_cneg<KY + K>(P[part], ny ^ nz);
+  }
+  const int sh = B > 64 * K - 2 ? B - (64 * K - 2) : 0;
+  const fx<KY + K> qr = ix_sar<KY + K>(P[0], sh), qi = ix_sar<KY + K>(P[1], sh);
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    Xr.w[w] = qr.w[w];
+    Xi.w[w] = qi.w[w];
+  }
+  t = sig + e + sh;
+}
+
+// (yr, yi) -= r x, with r x at scale 2^d relative to the units of y
+template <int K, int KY>
+__device__ __forceinline__ void bs_update(fx<KY> &yr, fx<KY> &yi, const fx<K> &rr, const fx<K> &ri,
+                                          const fx<K> &xr, const fx<K> &xi, int d, int *sFail) {
+  // re = rr xr - ri xi, im = rr xi + ri xr as 2K+1 limbs
+  fx<2 * K + 1> pr, pi;
+  {
+    uint64_t n1, n2, n3, n4;
+    ux<K> a1 = ix_abs<K>(rr, n1), b1 = ix_abs<K>(xr, n2);
+    ux<K> a2 = ix_abs<K>(ri, n3), b2 = ix_abs<K>(xi, n4);
+    ux<2 * K> p1 = ix_umul<K>(a1, b1), p2 = ix_umul<K>(a2, b2);
+    ux<2 * K> p3 = ix_umul<K>(a1, b2), p4 = ix_umul<K>(a2, b1);
+    fx<2 * K + 1> f1, f2, f3, f4;
+#pragma unroll
+    for (int w = 0; w < 2 * K; w++) {
+      f1.w[w] = p1.w[w];
+      f2.w[w] = p2.w[w];
+      f3.w[w] = p3.w[w];
+      f4.w[w] = p4.w[w];
+    }
+    f1.w[2 * K] = f2.w[2 * K] = f3.w[2 * K] = f4.w[2 * K] = 0;
+    ix_cneg<2 * K + 1>(f1, n1 ^ n2);
+    ix_cneg<2 * K + 1>(f2, n3 ^ n4);
+    ix_cneg<2 * K + 1>(f3, n1 ^ n4);
+    ix_cneg<2 * K + 1>(f4, n3 ^ n2);
+    pr = ix_sub<2 * K + 1>(f1, f2);
+    pi = ix_add<2 * K + 1>(f3, f4);
+  }
+  fx<KY> ur, ui;
+  if (d <= 0) {
+    const int s = -d;
+    if (s >= 64 * (2 * K + 1)) {
+      fx_zero<KY>(ur);
+      fx_zero<KY>(ui);
+    } else {
+      const fx<2 * K + 1> qr = ix_sar<2 * K + 1>(pr, s), qi = ix_sar<2 * K + 1>(pi, s);
+#pragma unroll
+      for (int w = 0; w < KY; w++) {
+        ur.w[w] = w < 2 * K + 1 ? qr.w[w] : (0 - (qr.w[2 * K] >> 63));
+        ui.w[w] = w < 2 * K + 1 ? qi.w[w] : (0 - (qi.w[2 * K] >> 63));
+      }
+    }
+  } else {
+    // a product larger than the units of y by 2^d: only harmless when tiny
+    if (ix_bitlen<2 * K + 1>(pr) + d > 64 * KY - 2 || ix_bitlen<2 * K + 1>(pi) + d > 64 * KY - 2)
+      *sFail = 1;
+#pragma unroll
+    for (int w = 0; w < KY; w++) {
+      ur.w[w] = w < 2 * K + 1 ? pr.w[w] : (0 - (pr.w[2 * K] >> 63));
+      ui.w[w] = w < 2 * K + 1 ? pi.w[w] : (0 - (pi.w[2 * K] >> 63));
+    }
+    // shift left by d (d < 64 KY guaranteed by the check above when it succeeds)
+    const int dd = d < 64 * KY ? d : 64 * KY - 1;
+    ur = ix_shl<KY>(ur, dd);
+    ui = ix_shl<KY>(ui, dd);
+  }
+  yr = ix_sub<KY>(yr, ur);
+  yi = ix_sub<KY>(yi, ui);
+}
+
+// shared memory of k_backsub_int for n unknowns
+template <int L>
+__host__ __device__ constexpr size_t bs_smem_bytes(int n) {
+  return sizeof(fx<L>) * 3 * (size_t)(n > 0 ? n : 1) + sizeof(int) * (3 * (size_t)n + 2);
+}
+
+template <int L, int ROWS>
+__global__ void __launch_bounds__(BS_MAX_THREADS) k_backsub_int(
+    const double *__restrict__ Rm, int64_t ldr, int32_t n, const double *__restrict__ Zs,
+    const double *__restrict__ sexp, double *__restrict__ dx, int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, KY = K + 2;
+  constexpr int D = (ROWS == 1 && L < 4) ? 3 : 2;  // levels of r_il held in registers
+  extern __shared__ __align__(16) unsigned char bsm[];
+  fx<K> *sX = (fx<K> *)bsm;          // [n][2] mantissas of x
+  fx<K> *sZ = sX + 2 * n;            // [n] mantissas of 1/r_ll
+  int *sT = (int *)(sZ + n);         // [n] exponents of x
+  int *sZe = sT + n;                 // [n] exponents of 1/r_ll
+  int *sS = sZe + n;                 // [n+1] column exponents
+  int *sFail = sS + n + 1;
+  if (*status != GN_OK) return;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) {
+    const uint64_t *z = (const uint64_t *)(Zs + (size_t)i * (K + 1));
+#pragma unroll
+    for (int w = 0; w < K; w++) sZ[i].w[w] = z[w];
+    sZe[i] = (int)Zs[(size_t)i * (K + 1) + K];
+    sS[i] = (int)sexp[i];
+  }
+  const int sig = (int)sexp[n];  // scale of y (the last column)
+  if (tid == 0) {
+    sS[n] = sig;
+    *sFail = 0;
+  }
+  fx<KY> Y[ROWS][2];
+#pragma unroll
+  for (int p = 0; p < ROWS; p++) {
+    const int i = tid + nt * p;
     if (i < n) {
       const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)n * ldr + i) * W);
       Y[p][0] = ix_widen<K, KY>(e[0]);
@@ -585,159 +699,85 @@ __global__ void __launch_bounds__(BS_THREADS) k_backsub_int(const double *__rest
       fx_zero<KY>(Y[p][1]);
     }
   }
-  if (tid == 0) sFail = 0;
+  // r_il of the next D levels in registers.  The level loop is unrolled by
+  // D so that every slot keeps its own registers: a load is consumed D - 1
+  // levels after it is issued and no register copy waits on it.
+  auto load_level = [&](int lv, fx<K>(&rr)[ROWS], fx<K>(&ri)[ROWS]) {
+#pragma unroll
+    for (int p = 0; p < ROWS; p++) {
+      const int i = tid + nt * p;
+      if (i < lv) {
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)lv * ldr + i) * W);
+#pragma unroll
+        for (int w = 0; w < K; w++) {
+          rr[p].w[w] = __ldg((const unsigned long long *)&e[0].w[w]);
+          ri[p].w[w] = __ldg((const unsigned long long *)&e[1].w[w]);
+        }
+      }
+    }
+  };
+  // level l: load level l - (D-1) into (nr, ni), subtract r_il x_l from the
+  // rows i < l with (rr, ri), the owner of row l-1 solves x_{l-1}; one barrier
+  auto level = [&](int l, const fx<K>(&rr)[ROWS], const fx<K>(&ri)[ROWS], fx<K>(&nr)[ROWS],
+                   fx<K>(&ni)[ROWS]) {
+    load_level(l - (D - 1), nr, ni);
+    const fx<K> xr = sX[2 * l], xi = sX[2 * l + 1];
+    const int d = sS[l] + sT[l] - sig;
+    // highest row first: for the owner of row l-1 that is row l-1 itself
+#pragma unroll
+    for (int p = ROWS - 1; p >= 0; p--) {
+      const int i = tid + nt * p;
+      if (i < l) {
+        bs_update<K, KY>(Y[p][0], Y[p][1], rr[p], ri[p], xr, xi, d, sFail);
+        if (i == l - 1) {
+          fx<K> Xr, Xi;
+          int t;
+          bs_solve<K, KY>(Y[p][0], Y[p][1], sZ[l - 1], sZe[l - 1], sig, Xr, Xi, t);
+          sX[2 * (l - 1)] = Xr;
+          sX[2 * (l - 1) + 1] = Xi;
+          sT[l - 1] = t;
+        }
+      }
+    }
+    __syncthreads();
+  };
+  fx<K> Ar[ROWS], Ai[ROWS], Br[ROWS], Bi[ROWS], Cr[ROWS], Ci[ROWS];
+  load_level(n - 1, Ar, Ai);
+  if (D == 3) load_level(n - 2, Br, Bi);
   __syncthreads();
-  for (int l = n - 1; l >= 0; l--) {
-    const int own = l % BS_THREADS, po = l / BS_THREADS;
-    // this level's r_il, loaded before x_l is known (hides the load latency)
-    fx<K> Rr[BS_ROWS], Ri[BS_ROWS];
+  // x_{n-1}
+  if (tid == (n - 1) % nt) {
+    const int po = (n - 1) / nt;
 #pragma unroll
-    for (int p = 0; p < BS_ROWS; p++) {
-      const int i = tid + BS_THREADS * p;
-      if (i < l) {
-        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)l * ldr + i) * W);
-        Rr[p] = e[0];
-        Ri[p] = e[1];
+    for (int p = 0; p < ROWS; p++)
+      if (p == po) {
+        fx<K> xr, xi;
+        int t;
+        bs_solve<K, KY>(Y[p][0], Y[p][1], sZ[n - 1], sZe[n - 1], sig, xr, xi, t);
+        sX[2 * (n - 1)] = xr;
+        sX[2 * (n - 1) + 1] = xi;
+        sT[n - 1] = t;
       }
-    }
-    const int sl = (int)sexp[l];
-    if (tid == own) {
-      // x_l = y_l * 2^sig * Z 2^e
-      const double *zs = Zs + (size_t)l * (K + 1);
-      fx<K> Z;
-#pragma unroll
-      for (int w = 0; w < K; w++) Z.w[w] = ((const uint64_t *)zs)[w];
-      const int e = (int)zs[K];
-      uint64_t nz;
-      const ux<K> uz = ix_abs<K>(Z, nz);
-      fx<KY + K> P[2];
-      int B = 0;
-#pragma unroll
-      for (int part = 0; part < 2; part++) {
-        fx<KY> y;
-#pragma unroll
-        for (int q = 0; q < BS_ROWS; q++)
-          if (q == po) y = Y[q][part];
-        uint64_t ny;
-        const ux<KY> uy = ix_abs<KY>(y, ny);
-        // |y| * |Z| as KY + K limbs
-#pragma unroll
-        for (int w = 0; w < KY + K; w++) P[part].w[w] = 0;
-#pragma unroll
-        for (int a = 0; a < KY; a++) {
-          u128_t carry = 0;
-#pragma unroll
-          for (int b = 0; b < K; b++) {
-            u128_t t = (u128_t)uy.w[a] * uz.w[b] + P[part].w[a + b] + carry;
-            P[part].w[a + b] = (uint64_t)t;
-            carry = t >> 64;
-          }
-          P[part].w[a + K] = (uint64_t)carry;
-        }
-        const int bl = ix_bitlen<KY + K>(P[part]);
-        B = bl > B ? bl : B;
-        ix_cneg<KY + K>(P[part], ny ^ nz);
-      }
-      const int sh = B > 64 * K - 2 ? B - (64 * K - 2) : 0;
-      fx<K> X[2];
-#pragma unroll
-      for (int part = 0; part < 2; part++) {
-        fx<KY + K> q = ix_sar<KY + K>(P[part], sh);
-#pragma unroll
-        for (int w = 0; w < K; w++) X[part].w[w] = q.w[w];
-      }
-      sX[0] = X[0];
-      sX[1] = X[1];
-      sT = sig + e + sh;
-      sXall[2 * l] = X[0];
-      sXall[2 * l + 1] = X[1];
-      sTall[l] = sig + e + sh;
-    }
-    __syncthreads();
-    const fx<K> xr = sX[0], xi = sX[1];
-    const int t = sT;
-#pragma unroll
-    for (int p = 0; p < BS_ROWS; p++) {
-      const int i = tid + BS_THREADS * p;
-      if (i < l) {
-        const fx<K> rr = Rr[p], ri = Ri[p];
-        // r_il x_l at scale s_l + t; in units of y: shift by d = s_l + t - sig
-        const int d = sl + t - sig;
-        // re = rr xr - ri xi, im = rr xi + ri xr as 2K+1 limbs
-        fx<2 * K + 1> pr, pi;
-        {
-          uint64_t n1, n2, n3, n4;
-          ux<K> a1 = ix_abs<K>(rr, n1), b1 = ix_abs<K>(xr, n2);
-          ux<K> a2 = ix_abs<K>(ri, n3), b2 = ix_abs<K>(xi, n4);
-          ux<2 * K> p1 = ix_umul<K>(a1, b1), p2 = ix_umul<K>(a2, b2);
-          ux<2 * K> p3 = ix_umul<K>(a1, b2), p4 = ix_umul<K>(a2, b1);
-          fx<2 * K + 1> f1, f2, f3, f4;
-#pragma unroll
-          for (int w = 0; w < 2 * K; w++) {
-            f1.w[w] = p1.w[w];
-            f2.w[w] = p2.w[w];
-            f3.w[w] = p3.w[w];
-            f4.w[w] = p4.w[w];
-          }
-          f1.w[2 * K] = f2.w[2 * K] = f3.w[2 * K] = f4.w[2 * K] = 0;
-          ix_cneg<2 * K + 1>(f1, n1 ^ n2);
-          ix_cneg<2 * K + 1>(f2, n3 ^ n4);
-          ix_cneg<2 * K + 1>(f3, n1 ^ n4);
-          ix_cneg<2 * K + 1>(f4, n3 ^ n2);
-          pr = ix_sub<2 * K + 1>(f1, f2);
-          pi = ix_add<2 * K + 1>(f3, f4);
-        }
-        fx<KY> ur, ui;
-        if (d <= 0) {
-          const int s = -d;
-          if (s >= 64 * (2 * K + 1)) {
-            fx_zero<KY>(ur);
-            fx_zero<KY>(ui);
-          } else {
-            fx<2 * K + 1> qr = ix_sar<2 * K + 1>(pr, s), qi = ix_sar<2 * K + 1>(pi, s);
-#pragma unroll
-            for (int w = 0; w < KY; w++) {
-              ur.w[w] = w < 2 * K + 1 ? qr.w[w] : (0 - (qr.w[2 * K] >> 63));
-              ui.w[w] = w < 2 * K + 1 ? qi.w[w] : (0 - (qi.w[2 * K] >> 63));
-            }
-          }
-        } else {
-          // a product larger than the units of y by 2^d: only harmless when tiny
-          if (ix_bitlen<2 * K + 1>(pr) + d > 64 * KY - 2 || ix_bitlen<2 * K + 1>(pi) + d > 64 * KY - 2) sFail = 1;
-          fx_zero<KY>(ur);
-          fx_zero<KY>(ui);
-#pragma unroll
-          for (int w = 0; w < KY; w++) {
-            ur.w[w] = w < 2 * K + 1 ? pr.w[w] : (0 - (pr.w[2 * K] >> 63));
-            ui.w[w] = w < 2 * K + 1 ? pi.w[w] : (0 - (pi.w[2 * K] >> 63));
-          }
-          // shift left by d (d < 64 KY guaranteed by the check above when it succeeds)
-          const int q = d >> 6, r = d & 63;
-          fx<KY> tr = ur, ti = ui;
-#pragma unroll
-          for (int w = KY - 1; w >= 0; w--) {
-            uint64_t lo_r = (w - q >= 0) ? tr.w[w - q] : 0, lo2_r = (w - q - 1 >= 0) ? tr.w[w - q - 1] : 0;
-            uint64_t lo_i = (w - q >= 0) ? ti.w[w - q] : 0, lo2_i = (w - q - 1 >= 0) ? ti.w[w - q - 1] : 0;
-            ur.w[w] = r ? ((lo_r << r) | (lo2_r >> (64 - r))) : lo_r;
-            ui.w[w] = r ? ((lo_i << r) | (lo2_i >> (64 - r))) : lo_i;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < BS_ROWS; q++)
-          if (q == p) {
-            Y[q][0] = ix_sub<KY>(Y[q][0], ur);
-            Y[q][1] = ix_sub<KY>(Y[q][1], ui);
-          }
-      }
-    }
-    __syncthreads();
   }
-  if (sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+  __syncthreads();
+  if constexpr (D == 3) {
+    for (int l = n - 1; l >= 1; l -= 3) {
+      level(l, Ar, Ai, Cr, Ci);
+      if (l - 1 >= 1) level(l - 1, Br, Bi, Ar, Ai);
+      if (l - 2 >= 1) level(l - 2, Cr, Ci, Br, Bi);
+    }
+  } else {
+    for (int l = n - 1; l >= 1; l -= 2) {
+      level(l, Ar, Ai, Br, Bi);
+      if (l - 1 >= 1) level(l - 1, Br, Bi, Ar, Ai);
+    }
+  }
+  if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
   // outputs: x_l = X 2^t as L-limb cascades
-  for (int l = tid; l < n; l += BS_THREADS) {
+  for (int l = tid; l < n; l += nt) {
     double cr[L], ci[L];
-    fx_to_cascade<K, L>(sXall[2 * l], -sTall[l], cr);
-    fx_to_cascade<K, L>(sXall[2 * l + 1], -sTall[l], ci);
+    fx_to_cascade<K, L>(sX[2 * l], -sT[l], cr);
+    fx_to_cascade<K, L>(sX[2 * l + 1], -sT[l], ci);
 #pragma unroll
     for (int q = 0; q < L; q++) {
       dx[(int64_t)l * W + q] = cr[q];

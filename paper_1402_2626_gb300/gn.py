@@ -32,8 +32,12 @@ STATUS = {0: "GN_OK", 1: "GN_EINVAL", 2: "GN_ENOMEM", 3: "GN_ECUDA", 4: "GN_ESIN
 REPORT_MAX = 64
 
 # exported symbols declared in include/gn.h
-SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_info", "gn_eval", "gn_lstsq",
-           "gn_newton", "gn_status_str", "gn_version", "gn_eval_noalloc")
+SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
+           "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_status_str", "gn_version",
+           "gn_eval_noalloc")
+# gn_arith: the faster per step (default), integer mantissas, or FP64
+# error-free transformations
+ARITH = {"auto": 0, "int": 1, "fp64": 2}
 
 
 class GnError(RuntimeError):
@@ -68,6 +72,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_system_create.restype = C.c_int
         L.gn_system_destroy.argtypes = [vp]
         L.gn_system_destroy.restype = C.c_int
+        L.gn_system_set_arith.argtypes = [vp, C.c_int]
+        L.gn_system_set_arith.restype = C.c_int
         L.gn_system_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i64p, i64p,
                                      C.POINTER(C.c_int32)]
         L.gn_system_info.restype = C.c_int
@@ -77,6 +83,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_eval_noalloc.restype = C.c_int
         L.gn_lstsq.argtypes = [vp, C.c_int, C.c_int32, C.c_int32, vp, C.c_int64, vp, vp, vp]
         L.gn_lstsq.restype = C.c_int
+        L.gn_mgs.argtypes = [vp, C.c_int, C.c_int32, C.c_int32, vp, C.c_int64, vp, vp, vp]
+        L.gn_mgs.restype = C.c_int
         L.gn_newton.argtypes = [vp, C.c_int, vp, C.c_int32, dp, C.POINTER(Report), vp]
         L.gn_newton.restype = C.c_int
         L.gn_status_str.argtypes = [C.c_int]
@@ -109,7 +117,7 @@ def _check(st: int, what: str):
 class System:
     """A polynomial system loaded into device memory (owns a gn_system)."""
 
-    def __init__(self, system: inputs.System, coef_limbs: int = 4):
+    def __init__(self, system: inputs.System, coef_limbs: int = 4, arith: str = "auto"):
         L = load_library()
         self.N, self.n, self.T = system.N, system.n, system.T
         self._keep = [np.ascontiguousarray(system.poly_ptr, np.int64),
@@ -128,6 +136,12 @@ class System:
         _check(st, "gn_system_create")
         self._h = h
         self._lib = L
+        self.set_arith(arith)
+
+    def set_arith(self, arith: str):
+        """Arithmetic of evaluation and least squares: "auto", "int" or "fp64" (gn_arith)."""
+        _check(self._lib.gn_system_set_arith(self._h, ARITH[arith]), "gn_system_set_arith")
+        self.arith = arith
 
     def close(self):
         if getattr(self, "_h", None):
@@ -164,6 +178,16 @@ class System:
         ncols, m = Ab.shape[0], Ab.shape[1]
         _check(self._lib.gn_lstsq(self._h, PREC[prec], m, ncols - 1, _ptr(Ab), m, _ptr(R), _ptr(dx),
                                   _stream(stream)), "gn_lstsq")
+
+    def mgs(self, prec, Ab, R, status, stream=None):
+        """MGS factorisation of Ab [n+1, m, 2, L] in place (no back substitution,
+        no synchronisation); R is an output and status a 1-element int32 CUDA
+        tensor that receives the device status."""
+        ncols, m = Ab.shape[0], Ab.shape[1]
+        if not status.is_cuda or str(status.dtype) != "torch.int32":
+            raise ValueError("status must be an int32 CUDA tensor")
+        _check(self._lib.gn_mgs(self._h, PREC[prec], m, ncols - 1, _ptr(Ab), m, _ptr(R),
+                                C.c_void_p(status.data_ptr()), _stream(stream)), "gn_mgs")
 
     def newton(self, prec, x, steps, tol=0.0, stream=None, raise_on_error=True):
         """``steps`` Gauss-Newton steps in place on x [n,2,L]; returns the report."""

@@ -1,7 +1,8 @@
 // Host harness for csrc/ifx.cuh (test support).  Reads lines
 // "op K a_0..a_{K-1} b_0..b_{K-1} [s]" (hex limbs, little-endian) and prints
 // the result limbs in hex.  ops: mul (ix_mul_shift), sq (ix_square),
-// add, sub, sar (by s), bitlen.
+// add, sub, sar (by s), bitlen; and "xsar N a_0..a_{N-1} s" / "xshl N ..."
+// (ix_sar / ix_shl on N-limb values, N = 1..5 or 9).
 #include <cstdio>
 #include <cstring>
 #include <cstdint>
@@ -40,10 +41,34 @@ static void run(const char *op) {
   printf("\n");
 }
 
+template <int N>
+static void run_shift(const char *op) {
+  gn::fx<N> a;
+  for (int i = 0; i < N; i++) scanf("%llx", (unsigned long long *)&a.w[i]);
+  int s = 0;
+  scanf("%d", &s);
+  gn::fx<N> r = !strcmp(op, "xsar") ? gn::ix_sar<N>(a, s) : gn::ix_shl<N>(a, s);
+  for (int i = 0; i < N; i++) printf("%llx ", (unsigned long long)r.w[i]);
+  printf("\n");
+}
+
 int main() {
   char op[16];
   int K;
   while (scanf("%15s %d", op, &K) == 2) {
+    if (op[0] == 'x') {
+      switch (K) {
+        case 1: run_shift<1>(op); break;
+        case 2: run_shift<2>(op); break;
+        case 3: run_shift<3>(op); break;
+        case 4: run_shift<4>(op); break;
+        case 5: run_shift<5>(op); break;
+        case 9: run_shift<9>(op); break;
+        default: return 2;
+      }
+      fflush(stdout);
+      continue;
+    }
     if (K == 1) run<1>(op);
     else if (K == 2) run<2>(op);
     else if (K == 4) run<4>(op);

@@ -78,3 +78,5 @@ def test_calls_reject_null_handles(lib):
     assert lib.gn_lstsq(None, 2, 4, 3, None, 4, None, None, None) == 1
     assert lib.gn_newton(None, 2, None, 1, 0.0, None, None) == 1
     assert lib.gn_system_destroy(None) == 1
+    assert lib.gn_system_set_arith(None, 0) == 1
+    assert lib.gn_mgs(None, 2, 4, 3, None, 4, None, None, None) == 1

@@ -3,7 +3,7 @@
 The same source that the kernels use for exact sums is compiled for the host
 (nvcc, no GPU needed) and checked against exact rational sums: the sum of
 the addends, truncated below 2^-F per addend, converted to a cascade of L
-doubles each truncated to 53 bits.
+doubles, each the double nearest to what the limbs before it leave over.
 """
 
 import os
@@ -74,11 +74,14 @@ def test_sums_exact(harness, NL, L, F):
         assert ok == 1
         exact = sum((_truncate(Fraction(v), F_) for v in vals if abs(v) >= 2.0 ** -1022), Fraction(0))
         got = sum((Fraction(o) for o in out), Fraction(0))
-        # the cascade is exact up to the truncation of its last limb
-        assert abs(got - exact) <= abs(exact) * Fraction(2) ** (-52 * L_) + Fraction(2) ** -F_
-        # limbs are nonoverlapping and carry the sign of the value
+        # the cascade is exact up to the rounding of its last limb
+        assert abs(got - exact) <= abs(exact) * Fraction(2) ** (-53 * L_ + 1) + Fraction(2) ** -F_
+        # limbs are nonoverlapping: each at most half an ulp of the one before
         for a, b in zip(out, out[1:]):
-            assert b == 0 or abs(b) < abs(a) * 2.0 ** -52
+            assert b == 0 or abs(b) <= abs(a) * 2.0 ** -53
+        # the leading limb is the double nearest to the whole value
+        if exact != 0:
+            assert abs(Fraction(out[0]) - exact) <= abs(Fraction(out[0])) * Fraction(2) ** -53 * (1 + Fraction(2) ** -50)
 
 
 def test_overflow_reported(harness):

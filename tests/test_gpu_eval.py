@@ -17,6 +17,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PRECS = [("d", 1), ("dd", 2), ("qd", 4)]
+# integer-mantissa evaluation (default) and FP64 error-free transformations
+ARITHS = ["int", "fp64"]
 
 
 def _gn():
@@ -26,9 +28,9 @@ def _gn():
     return gn
 
 
-def gpu_eval(system, x, L, prec):
+def gpu_eval(system, x, L, prec, arith="int"):
     gn = _gn()
-    s = gn.System(system)
+    s = gn.System(system, arith=arith)
     xd = torch.tensor(np.ascontiguousarray(x[..., :L]), device="cuda")
     f = torch.full((system.N, 2, L), np.nan, dtype=torch.float64, device="cuda")
     J = torch.full((system.n, system.N, 2, L), np.nan, dtype=torch.float64, device="cuda")
@@ -39,8 +41,8 @@ def gpu_eval(system, x, L, prec):
     return out
 
 
-def check(system, x, L, prec, rows=None):
-    f, J = gpu_eval(system, x, L, prec)
+def check(system, x, L, prec, rows=None, arith="int"):
+    f, J = gpu_eval(system, x, L, prec, arith)
     r0, r1 = (0, system.N) if rows is None else rows
     fo, Jo, _ = oracle.evaluate(system, x, L, "reverse", rows=(r0, r1), nthreads=8)
     Sf, SJ = term_scales(system, x, rows=(r0, r1))
@@ -55,8 +57,9 @@ def check(system, x, L, prec, rows=None):
     return float((ef / np.maximum(Sf, 1e-300)).max()), float((eJ[~zero] / SJ[~zero]).max())
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_edge_cases(prec, L):
+def test_edge_cases(prec, L, arith):
     # one variable; constant-only polynomial; k = 1; a variable in no term
     # (zero column); long supports (k up to 40) and high exponents (7)
     cases = [
@@ -73,29 +76,32 @@ def test_edge_cases(prec, L):
                                exp=s.exp, coef=s.coef, xstar=x5, x0=x5))
     for sys_ in cases:
         x = sys_.point("x0", L)
-        check(sys_, x, L, prec)
+        check(sys_, x, L, prec, arith=arith)
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_gn32_full(prec, L):
+def test_gn32_full(prec, L, arith):
     s = inputs.workload("gn32")
-    check(s, s.point("x0", L), L, prec)
+    check(s, s.point("x0", L), L, prec, arith=arith)
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_ragged_many_tiles(prec, L):
+def test_ragged_many_tiles(prec, L, arith):
     # T not a multiple of the 128-thread CTA, N not a multiple of 4 warps
     s = inputs.random_system(37, 29, (20, 45), (1, 14), 5, seed=77)
-    check(s, s.point("x0", L), L, prec)
+    check(s, s.point("x0", L), L, prec, arith=arith)
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_gn256_sampled_rows(prec, L):
+def test_gn256_sampled_rows(prec, L, arith):
     """Full-size workload (n = N = 256, 256 terms of 16 variables per
     polynomial, exponents 1..5), sampled rows checked one by one."""
     s = inputs.workload("gn256")
     x = s.point("x0", L)
-    f, J = gpu_eval(s, x, L, prec)
+    f, J = gpu_eval(s, x, L, prec, arith)
     tol = PARITY_TOL[L]
     for i in (0, 1, 127, 200, 255):
         fo, Jo, _ = oracle.evaluate(s, x, L, "reverse", rows=(i, i + 1), nthreads=8)
@@ -106,17 +112,19 @@ def test_gn256_sampled_rows(prec, L):
         assert not np.any(J[i:i + 1][~nz])
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_deterministic(prec, L):
+def test_deterministic(prec, L, arith):
     s = inputs.random_system(16, 16, 20, (2, 9), 4, seed=9)
-    a = gpu_eval(s, s.point("x0", L), L, prec)
-    b = gpu_eval(s, s.point("x0", L), L, prec)
+    a = gpu_eval(s, s.point("x0", L), L, prec, arith)
+    b = gpu_eval(s, s.point("x0", L), L, prec, arith)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
-def test_root_residual_dd():
+@pytest.mark.parametrize("arith", ARITHS)
+def test_root_residual_dd(arith):
     """At the built-in root f vanishes to DD level (Section 5 setting)."""
     s = inputs.workload("gn32")
-    f, _ = gpu_eval(s, s.point("xstar", 2), 2, "dd")
+    f, _ = gpu_eval(s, s.point("xstar", 2), 2, "dd", arith)
     Sf, _ = term_scales(s, s.point("xstar", 2))
     assert np.all(limb_diff(f, np.zeros_like(f)) <= 1e-28 * Sf)

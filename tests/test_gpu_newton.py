@@ -12,6 +12,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 PRECS = [("d", 1), ("dd", 2), ("qd", 4)]
+# integer mantissas (default) and FP64 error-free transformations
+ARITHS = ["int", "fp64"]
 
 
 def _gn():
@@ -30,11 +32,11 @@ def _rand_matrix(rng, m, ncols, L):
     return A
 
 
-def gpu_lstsq(A, L, prec):
+def gpu_lstsq(A, L, prec, arith="int"):
     gn = _gn()
     m, ncols = A.shape[0], A.shape[1]
     # any system provides the workspace handle
-    s = gn.System(inputs.random_system(2, 2, 2, 1, 1, seed=0))
+    s = gn.System(inputs.random_system(2, 2, 2, 1, 1, seed=0), arith=arith)
     Ab = torch.tensor(np.ascontiguousarray(A.transpose(1, 0, 2, 3)), device="cuda")
     R = torch.zeros((ncols, ncols, 2, L), dtype=torch.float64, device="cuda")
     dx = torch.zeros((ncols - 1, 2, L), dtype=torch.float64, device="cuda")
@@ -47,12 +49,13 @@ def gpu_lstsq(A, L, prec):
             dx.cpu().numpy())
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
 @pytest.mark.parametrize("m,n", [(1, 1), (7, 4), (40, 33), (300, 257), (513, 60)])
-def test_lstsq_parity(prec, L, m, n):
+def test_lstsq_parity(prec, L, m, n, arith):
     rng = np.random.default_rng(m * 1000 + n)
     A = _rand_matrix(rng, m, n + 1, L)
-    Q, R, dx = gpu_lstsq(A, L, prec)
+    Q, R, dx = gpu_lstsq(A, L, prec, arith)
     Qo, Ro = oracle.mgs(A, L, nthreads=8)
     dxo = oracle.backsub(Ro, L)
     tol = PARITY_TOL[L]
@@ -66,23 +69,71 @@ def test_lstsq_parity(prec, L, m, n):
 
 
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_lstsq_singular(prec, L):
+def test_lstsq_parity_two_rows_per_thread(prec, L):
+    """n = 600 > 512: back substitution with two rows per thread."""
+    rng = np.random.default_rng(600)
+    m, n = 620, 600
+    A = _rand_matrix(rng, m, n + 1, L)
+    Q, R, dx = gpu_lstsq(A, L, prec)
+    Qo, Ro = oracle.mgs(A, L, nthreads=16)
+    dxo = oracle.backsub(Ro, L)
+    tol = PARITY_TOL[L]
+    cn = np.sqrt((A[..., 0] ** 2).sum(axis=(0, 2)))
+    assert np.all(limb_diff(R, Ro) <= tol * cn[None, :] * 10)
+    scale = np.abs(dxo[:, :, 0]).max()
+    assert np.all(limb_diff(dx, dxo) <= tol * 1000 * max(scale, 1.0))
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("prec,L", PRECS)
+@pytest.mark.parametrize("m,n", [(40, 33), (256, 256)])
+def test_mgs_factorisation_only(prec, L, m, n, arith):
+    """gn_mgs: the factorisation of gn_lstsq, asynchronous, status on the device."""
+    gn = _gn()
+    rng = np.random.default_rng(m * 7 + n)
+    A = _rand_matrix(rng, m, n + 1, L)
+    s = gn.System(inputs.random_system(n, n, 2, 1, 1, seed=0), arith=arith)
+    Ab = torch.tensor(np.ascontiguousarray(A.transpose(1, 0, 2, 3)), device="cuda")
+    R = torch.zeros((n + 1, n + 1, 2, L), dtype=torch.float64, device="cuda")
+    st = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    s.mgs(prec, Ab, R, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Q, Rg = Ab.cpu().numpy().transpose(1, 0, 2, 3), R.cpu().numpy().transpose(1, 0, 2, 3)
+    Qo, Ro = oracle.mgs(A, L, nthreads=8)
+    tol = PARITY_TOL[L]
+    cn = np.sqrt((A[..., 0] ** 2).sum(axis=(0, 2)))
+    assert np.all(limb_diff(Rg, Ro) <= tol * cn[None, :] * 10)
+    assert np.all(limb_diff(Q[:, :n], Qo[:, :n]) <= tol * 10)
+    # a repeated column: the status word reports the rank deficiency
+    A[:, 2] = A[:, 0]
+    Ab.copy_(torch.tensor(np.ascontiguousarray(A.transpose(1, 0, 2, 3))))
+    s.mgs(prec, Ab, R, st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 4
+    s.close()
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("prec,L", PRECS)
+def test_lstsq_singular(prec, L, arith):
     gn = _gn()
     rng = np.random.default_rng(5)
     A = _rand_matrix(rng, 9, 5, L)
     A[:, 2] = A[:, 0]
     with pytest.raises(gn.GnError) as e:
-        gpu_lstsq(A, L, prec)
+        gpu_lstsq(A, L, prec, arith)
     assert e.value.status == 4
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_newton_gn32_parity(prec, L):
+def test_newton_gn32_parity(prec, L, arith):
     """Four steps from x* + 1e-6 (the plain Gauss-Newton workload): the GPU
     iterates match the oracle's and converge quadratically to x*."""
     gn = _gn()
     s = inputs.workload("gn32")
-    sysg = gn.System(s)
+    sysg = gn.System(s, arith=arith)
     x = torch.tensor(s.point("x0", L), device="cuda")
     xo = s.point("x0", L)
     tol = PARITY_TOL[L]
@@ -124,12 +175,13 @@ def test_newton_multi_step_report(prec, L):
     sysg.close()
 
 
-def test_newton_gn256_dd_step_parity():
+@pytest.mark.parametrize("arith", ARITHS)
+def test_newton_gn256_dd_step_parity(arith):
     """One full-size step in double double (n = N = 256, 65,792 terms)."""
     gn = _gn()
     L = 2
     s = inputs.workload("gn256")
-    sysg = gn.System(s)
+    sysg = gn.System(s, arith=arith)
     x = torch.tensor(s.point("x0", L), device="cuda")
     sysg.newton("dd", x, 1)
     xo, _, _, _ = oracle.newton_step(s, s.point("x0", L), L, nthreads=16)
@@ -137,12 +189,13 @@ def test_newton_gn256_dd_step_parity():
     sysg.close()
 
 
+@pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-def test_newton_gn256_converges(prec, L):
+def test_newton_gn256_converges(prec, L, arith):
     """Property at full size: quadratic convergence to the built-in root."""
     gn = _gn()
     s = inputs.workload("gn256")
-    sysg = gn.System(s)
+    sysg = gn.System(s, arith=arith)
     x = torch.tensor(s.point("x0", L), device="cuda")
     rep = sysg.newton(prec, x, 4)
     d = x.cpu().numpy()
@@ -166,4 +219,23 @@ def test_newton_singular_reports():
     rep = sysg.newton("dd", x, 3, raise_on_error=False)
     assert rep["status"] == 4 and rep["steps_done"] == 0
     assert torch.equal(x, x_before)  # no update was applied
+    sysg.close()
+
+
+def test_arith_switch_rebuilds_step():
+    """Switching the arithmetic between runs on the same x pointer discards
+    the captured step: each run matches the oracle's iterates."""
+    gn = _gn()
+    L = 2
+    s = inputs.workload("gn32")
+    sysg = gn.System(s)
+    x = torch.tensor(s.point("x0", L), device="cuda")
+    xo = s.point("x0", L)
+    for arith in ("auto", "int", "fp64", "auto"):
+        sysg.set_arith(arith)
+        sysg.newton("dd", x, 1)
+        xo, _, _, _ = oracle.newton_step(s, xo, L, nthreads=8)
+        assert np.all(limb_diff(x.cpu().numpy(), xo) <= PARITY_TOL[L]), arith
+    assert sysg._lib.gn_system_set_arith(sysg._h, 7) == 1  # unknown value: GN_EINVAL
+    assert sysg._lib.gn_system_set_arith(sysg._h, -1) == 1
     sysg.close()

@@ -97,6 +97,26 @@ def test_square_add_sub_sar_bitlen(harness, K):
             assert val(got) == want, kind
 
 
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 9])
+def test_barrel_shifts(harness, N):
+    """ix_sar (arithmetic) and ix_shl (bits above 64 N lost) for every shift
+    0 <= s < 64 N at the widths the kernels use (K, K+1, 2K+1, 3K+2 limbs)."""
+    rng = np.random.default_rng(90 + N)
+    lines, exp = [], []
+    mod = 1 << (64 * N)
+    shifts = list(range(0, 64 * N, 7 if N > 2 else 1)) + [64 * N - 1, 63, 64, 65]
+    for s in shifts:
+        if s >= 64 * N:
+            continue
+        a = rand_signed(rng, N)
+        lines.append(f"xsar {N} " + " ".join("%x" % x for x in limbs(a, N)) + f" {s}")
+        exp.append(a >> s)
+        lines.append(f"xshl {N} " + " ".join("%x" % x for x in limbs(a, N)) + f" {s}")
+        exp.append(val(limbs((a << s) % mod, N)))
+    for want, got in zip(exp, run(harness, lines)):
+        assert val(got) == want
+
+
 @pytest.mark.parametrize("K", [1, 2, 4])
 def test_rsqrt_frac(harness, K):
     """Y = 2^(64K-2)/sqrt(t) for t = tt/2^(64K) in [1/4, 1), to within a few units."""

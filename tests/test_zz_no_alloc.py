@@ -38,7 +38,7 @@ def _buffers(system, L):
 def test_noalloc_matches_gn_eval_twice(prec, L):
     gn = _gn()
     for system in (inputs.workload("gn32"), inputs.random_system(37, 29, (20, 45), (1, 14), 5, seed=77)):
-        s = gn.System(system)
+        s = gn.System(system, arith="fp64")  # the arithmetic gn_eval_noalloc uses
         x = torch.tensor(system.point("x0", L), device="cuda")
         f_ref, J_ref = _buffers(system, L)
         s.eval(prec, x, f_ref, J_ref)
@@ -78,7 +78,7 @@ def test_noalloc_allocates_nothing():
 def test_noalloc_full_size_and_limit():
     gn = _gn()
     system = inputs.workload("gn256")  # 65,792 terms, 1,048,576 occurrences
-    s = gn.System(system)
+    s = gn.System(system, arith="fp64")  # the arithmetic gn_eval_noalloc uses
     x = torch.tensor(system.point("x0", 2), device="cuda")
     f_ref, J_ref = _buffers(system, 2)
     s.eval("dd", x, f_ref, J_ref)
