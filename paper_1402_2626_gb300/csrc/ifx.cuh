@@ -243,13 +243,92 @@ FX_HD fx<N> ix_shl(const fx<N> &a, int s) {
   return o;
 }
 
+// One Newton step y <- y + y (1 - t y^2) / 2 for y ~ 1/sqrt(t) in K-limb
+// fixed point: Y = y 2^(64K-2), tt = t 2^(64K) with t in [1/4, 1).  The
+// number of correct bits roughly doubles, up to the resolution of K limbs.
+template <int K>
+FX_HD void ix_rsqrt_step(const ux<K> &tt, ux<K> &Y) {
+  constexpr int S = 64 * K - 2;
+  // W = Y^2 / 2^S  (value y^2, scale 2^S), K+1 limbs
+  ux<2 * K> y2 = ix_umul<K>(Y, Y);
+  ux<K + 1> Wv;
+#pragma unroll
+  for (int t = 0; t <= K; t++) {
+    uint64_t lo = y2.w[K - 1 + t] >> 62;
+    uint64_t hi = (K + t < 2 * K) ? (y2.w[K + t] << 2) : 0;
+    Wv.w[t] = lo | hi;
+  }
+  // V = t * W = tt * W / 2^(64K)  (value t y^2 ~ 1, scale 2^S)
+  ux<K> Wk;
+#pragma unroll
+  for (int i = 0; i < K; i++) Wk.w[i] = Wv.w[i];
+  ux<2 * K> tw = ix_umul<K>(tt, Wk);
+  // tw / 2^(64K): limbs K..2K-1, plus tt * Wv.w[K] (W's top limb) at weight 2^(64K)
+  ux<K> V;
+#pragma unroll
+  for (int i = 0; i < K; i++) V.w[i] = tw.w[K + i];
+  {
+    u128_t c = 0;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+      c += (u128_t)V.w[i] + (u128_t)tt.w[i] * Wv.w[K];
+      V.w[i] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  // e = 2^S - V (signed, small), Y <- Y + Y e / 2^(S+1)
+  fx<K> one;
+#pragma unroll
+  for (int i = 0; i < K; i++) one.w[i] = (i == (S >> 6)) ? (1ull << (S & 63)) : 0;
+  fx<K> Vf;
+#pragma unroll
+  for (int i = 0; i < K; i++) Vf.w[i] = V.w[i];
+  fx<K> e = ix_sub<K>(one, Vf);
+  uint64_t ne;
+  ux<K> ue = ix_abs<K>(e, ne);
+  ux<2 * K> ye = ix_umul<K>(Y, ue);
+  // ye / 2^(S+1) = ye >> (64K - 1)
+  fx<K> d;
+#pragma unroll
+  for (int t = 0; t < K; t++) {
+    uint64_t lo = ye.w[K - 1 + t] >> 63;
+    uint64_t hi = (K + t < 2 * K) ? (ye.w[K + t] << 1) : 0;
+    d.w[t] = lo | hi;
+  }
+  ix_cneg<K>(d, ne);
+  fx<K> Yf;
+#pragma unroll
+  for (int i = 0; i < K; i++) Yf.w[i] = Y.w[i];
+  Yf = ix_add<K>(Yf, d);
+#pragma unroll
+  for (int i = 0; i < K; i++) Y.w[i] = Yf.w[i];
+}
+
+// the top KK limbs of tt, and Y from KK to 2 KK limbs (same value)
+template <int K, int KK>
+FX_HD ux<KK> ix_top(const ux<K> &tt) {
+  ux<KK> r;
+#pragma unroll
+  for (int i = 0; i < KK; i++) r.w[i] = tt.w[K - KK + i];
+  return r;
+}
+
+template <int KK>
+FX_HD ux<2 * KK> ix_rsqrt_widen(const ux<KK> &Y) {
+  ux<2 * KK> r;
+#pragma unroll
+  for (int i = 0; i < 2 * KK; i++) r.w[i] = i < KK ? 0 : Y.w[i - KK];
+  return r;
+}
+
 // Y = 2^(64K-2) / sqrt(t) for t = tt / 2^(64K) in [1/4, 1), tt a K-limb
-// unsigned fraction: FP32 reciprocal square root seed, then Newton steps
-// y <- y + y (1 - t y^2) / 2 in K-limb fixed point (precision doubles per
-// step: 24 -> 48 -> 96 -> 192 -> 384 bits).  Y is in (2^(64K-2), 2^(64K-1)].
+// unsigned fraction: FP32 reciprocal square root seed (24 bits), then Newton
+// steps, each in as many limbs as its result needs: 1 limb (48 bits), then
+// 1 more (K = 1) or 2 limbs (96 bits), then K limbs until K limbs are full.
+// Y is in (2^(64K-2), 2^(64K-1)].
 template <int K>
 FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
-  constexpr int S = 64 * K - 2;
+  static_assert(K == 1 || K == 2 || K == 4, "K = 1, 2 or 4 limbs");
   // seed from the top 32 bits of t
   const float tf = (float)(uint32_t)(tt.w[K - 1] >> 32) * 2.3283064365386963e-10f;  // 2^-32
 #if defined(__CUDA_ARCH__)
@@ -257,80 +336,28 @@ FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
 #else
   const float y0 = 1.0f / __builtin_sqrtf(tf);
 #endif
-  // Y0 = y0 2^S as K limbs: y0 in (1, 2] has 24 significant bits
-  ux<K> Y;
-#pragma unroll
-  for (int i = 0; i < K; i++) Y.w[i] = 0;
-  {
-    const uint64_t m = (uint64_t)(y0 * 16777216.0f);  // y0 2^24, < 2^26
-    // place m 2^(S - 24)
-    const int sh = S - 24, q = sh >> 6, r = sh & 63;
-#pragma unroll
-    for (int i = 0; i < K; i++) {
-      uint64_t v = 0;
-      if (i == q) v = m << r;
-      if (i == q + 1 && r) v = m >> (64 - r);
-      Y.w[i] = v;
+  // y0 in (1, 2] with 24 significant bits, as one limb at scale 2^62
+  ux<1> Y1;
+  Y1.w[0] = (uint64_t)(y0 * 16777216.0f) << 38;
+  const ux<1> t1 = ix_top<K, 1>(tt);
+  ix_rsqrt_step<1>(t1, Y1);  // ~48 bits
+  if constexpr (K == 1) {
+    ix_rsqrt_step<1>(t1, Y1);
+    return Y1;
+  } else {
+    ux<2> Y2 = ix_rsqrt_widen<1>(Y1);
+    const ux<2> t2 = ix_top<K, 2>(tt);
+    ix_rsqrt_step<2>(t2, Y2);  // ~96 bits
+    if constexpr (K == 2) {
+      ix_rsqrt_step<2>(t2, Y2);
+      return Y2;
+    } else {
+      ux<4> Y4 = ix_rsqrt_widen<2>(Y2);
+      ix_rsqrt_step<4>(tt, Y4);  // ~192 bits
+      ix_rsqrt_step<4>(tt, Y4);
+      return Y4;
     }
   }
-  constexpr int ITERS = (K == 1) ? 2 : (K == 2 ? 3 : 4);
-#pragma unroll
-  for (int it = 0; it < ITERS; it++) {
-    // W = Y^2 / 2^S  (value y^2, scale 2^S), K+1 limbs
-    ux<2 * K> y2 = ix_umul<K>(Y, Y);
-    ux<K + 1> Wv;
-#pragma unroll
-    for (int t = 0; t <= K; t++) {
-      uint64_t lo = y2.w[K - 1 + t] >> 62;
-      uint64_t hi = (K + t < 2 * K) ? (y2.w[K + t] << 2) : 0;
-      Wv.w[t] = lo | hi;
-    }
-    // V = t * W = tt * W / 2^(64K)  (value t y^2 ~ 1, scale 2^S)
-    ux<K> Wk;
-#pragma unroll
-    for (int i = 0; i < K; i++) Wk.w[i] = Wv.w[i];
-    ux<2 * K> tw = ix_umul<K>(tt, Wk);  // W's top limb (<= 4 in value) handled below
-    // tw / 2^(64K): limbs K..2K-1, plus tt * Wv.w[K] (W's top limb) at weight 2^(64K)
-    ux<K> V;
-#pragma unroll
-    for (int i = 0; i < K; i++) V.w[i] = tw.w[K + i];
-    {
-      u128_t c = 0;
-#pragma unroll
-      for (int i = 0; i < K; i++) {
-        c += (u128_t)V.w[i] + (u128_t)tt.w[i] * Wv.w[K];
-        V.w[i] = (uint64_t)c;
-        c >>= 64;
-      }
-    }
-    // e = 2^S - V (signed, small), Y <- Y + Y e / 2^(S+1)
-    fx<K> one;
-#pragma unroll
-    for (int i = 0; i < K; i++) one.w[i] = (i == (S >> 6)) ? (1ull << (S & 63)) : 0;
-    fx<K> Vf;
-#pragma unroll
-    for (int i = 0; i < K; i++) Vf.w[i] = V.w[i];
-    fx<K> e = ix_sub<K>(one, Vf);
-    uint64_t ne;
-    ux<K> ue = ix_abs<K>(e, ne);
-    ux<2 * K> ye = ix_umul<K>(Y, ue);
-    // ye / 2^(S+1) = ye >> (64K - 1): limbs (K-1).. with shift 63
-    fx<K> d;
-#pragma unroll
-    for (int t = 0; t < K; t++) {
-      uint64_t lo = ye.w[K - 1 + t] >> 63;
-      uint64_t hi = (K + t < 2 * K) ? (ye.w[K + t] << 1) : 0;
-      d.w[t] = lo | hi;
-    }
-    ix_cneg<K>(d, ne);
-    fx<K> Yf;
-#pragma unroll
-    for (int i = 0; i < K; i++) Yf.w[i] = Y.w[i];
-    Yf = ix_add<K>(Yf, d);
-#pragma unroll
-    for (int i = 0; i < K; i++) Y.w[i] = Yf.w[i];
-  }
-  return Y;
 }
 
 }  // namespace gn

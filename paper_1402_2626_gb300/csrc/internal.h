@@ -86,6 +86,9 @@ gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, 
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                              const double *rinv, double *dx, int32_t *status, cudaStream_t st);
 constexpr int BACKSUB_INT_MAX_N = 1024;
+// R and 1/r_kk as cascades from the mantissas the MGS launch left
+gn_status launch_mgs_r_out(int L, double *R, const double *Rm, int64_t ldr, int32_t ncols,
+                           double *rinv, const int32_t *status, cudaStream_t st);
 gn_status launch_mgs_to_cascade(int L, double *A, int32_t m, int64_t lda, int32_t ncols,
                                 const double *rinv, const int32_t *status, cudaStream_t st);
 // doubles of the per-solve scratch: 1/r_kk (L per column), original norms, column exponents

@@ -249,14 +249,17 @@ static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64
                             double *dx, int32_t *status, cudaStream_t st, bool want_q) {
   const int32_t ncols = n + 1;
   const int64_t ldr = ncols;
-  if (cudaMemsetAsync(R, 0, sizeof(double) * 2 * L * ldr * ncols, st) != cudaSuccess) return GN_ECUDA;
-  if (use_int && flags && mgs_flow_clusters(L) > 0 && mgs_flow_fits(L, m, ncols)) {
-    const bool int_bs = dx && Rm && Zs && n <= BACKSUB_INT_MAX_N;
-    gn_status e = launch_mgs_flow(L, A, m, lda, ncols, R, ldr, rinv, flags, status,
-                                  int_bs ? Rm : nullptr, int_bs ? Zs : nullptr, st);
+  if (use_int && flags && Rm && Zs && mgs_flow_clusters(L) > 0 && mgs_flow_fits(L, m, ncols)) {
+    const bool int_bs = dx && n <= BACKSUB_INT_MAX_N;
+    gn_status e = launch_mgs_flow(L, A, m, lda, ncols, R, ldr, rinv, flags, status, Rm, Zs, st);
     if (e) return e;
     if (want_q) {
       e = launch_mgs_to_cascade(L, A, m, lda, ncols, rinv, status, st);
+      if (e) return e;
+    }
+    // R as cascades: for the caller, or for the FP64 back substitution
+    if (want_q || (dx && !int_bs)) {
+      e = launch_mgs_r_out(L, R, Rm, ldr, ncols, rinv, status, st);
       if (e) return e;
     }
     if (!dx) return GN_OK;
@@ -264,6 +267,7 @@ static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64
     k_backsub<L><<<1, MGS_THREADS, 0, st>>>(R, ldr, n, rinv, dx, status);
     return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
   }
+  if (cudaMemsetAsync(R, 0, sizeof(double) * 2 * L * ldr * ncols, st) != cudaSuccess) return GN_ECUDA;
   // one launch per pivot and one per trailing update (devices without clusters)
   k_colnorms<L><<<ncols, 128, 0, st>>>(A, m, lda, ncols, nrm0);
   for (int k = 0; k < ncols; k++) {

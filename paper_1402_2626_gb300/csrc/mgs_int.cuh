@@ -10,116 +10,181 @@
 //   A_ij <- A_ij - D_kj Q_ik / 2^(64K-2)
 //   T_j  = sum_i |A_ij|^2 (exact)                 (r_jj = sqrt(T_j) 2^s_j)
 //   Q_ij = A_ij Z_j / 2^(b_j - 1),  Z_j ~ 2^(b_j + 64K - 3) / sqrt(T_j)
-// The reciprocal square root comes from the double rsqrt and one or two
-// Newton steps (FP64 TwoProd pieces, exact integer sums).
+// The reciprocal square root comes from an FP32 seed and integer Newton
+// steps (ifx.cuh).
 #pragma once
 
 namespace gn {
 
-// 1 / sqrt(s) for a positive cascade s of L limbs, to about 2^(-52 L)
-// relative: rsqrt seed, then Newton y <- y - y (s y^2 - 1) / 2 with the
-// residual s y^2 - 1 summed exactly (its leading bits cancel).
-template <int L>
-__device__ void rsqrt_cascade(const double (&s)[L], double (&y)[L]) {
-#pragma unroll
-  for (int l = 0; l < L; l++) y[l] = 0.0;
-  double y0 = rsqrt(s[0]);
-  if constexpr (L == 1) {
-    // one Newton step in double: y (3 - s y^2) / 2
-    double h = __fma_rn(-s[0] * y0, y0, 1.0);
-    y[0] = __fma_rn(0.5 * y0, h, y0);
-    return;
-  } else {
-    // step 1 (to ~104 bits): y1 = y0 - y0 d / 2, d = s y0^2 - 1
-    double p, e;
-    two_prod(y0, y0, p, e);
-    double d = __fma_rn(s[0], p, -1.0);
-    d = __fma_rn(s[0], e, d);
-    d = __fma_rn(s[1], p, d);
-    double c = -0.5 * y0 * d;
-    double y1h, y1l;
-    fast_two_sum(y0, c, y1h, y1l);
-    if constexpr (L == 2) {
-      y[0] = y1h;
-      y[1] = y1l;
-      return;
-    } else {
-      // step 2 (to ~208 bits) with exact sums: d = s y1^2 - 1, y2 = y1 - y1 d / 2
-      constexpr int NL = 5;
-      const int F = 290;  // values near 1
-      double q[4] = {y1h, y1l, 0.0, 0.0};
-      fx<NL> acc;
-      fx_zero<NL>(acc);
-      fx_add_prod<4, NL>(acc, q, q, false, F);
-      double y2c[4];
-      fx_to_cascade<NL, 4>(acc, F, y2c);  // y1^2
-      fx_zero<NL>(acc);
-      fx_add_prod<4, NL>(acc, s, y2c, false, F);
-      fx_add_bits<NL>(acc, fx_dbits(1.0) ^ 0x8000000000000000ull, F);
-      double dd[4];
-      fx_to_cascade<NL, 4>(acc, F, dd);  // d ~ 2^-104, about 186 bits above the resolution
-      // y2 = y1 - y1 d / 2
-      fx_zero<NL>(acc);
-      fx_add_limbs<4, NL>(acc, q, false, F);
-      double hd[4] = {0.5 * dd[0], 0.5 * dd[1], 0.5 * dd[2], 0.5 * dd[3]};
-      fx_add_prod<4, NL>(acc, q, hd, true, F);
-      fx_to_cascade<NL, 4>(acc, F, y);
+// ---- messages between the CTAs of a cluster ----
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// the cluster address of this CTA's shared location a in the CTA of rank r
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t a, uint32_t r) {
+  uint32_t d;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(r));
+  return d;
+}
+
+__device__ __forceinline__ void mb_init(uint64_t *bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+}
+
+// this CTA's arrival for the current phase, announcing `bytes` to come
+__device__ __forceinline__ void mb_expect(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 8 bytes to the cluster address ra; completes 8 bytes of the transaction
+// count of the mbarrier at cluster address rb
+__device__ __forceinline__ void st_async8(uint32_t ra, uint64_t v, uint32_t rb) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.u64 [%0], %1, [%2];" ::"r"(ra),
+               "l"(v), "r"(rb)
+               : "memory");
+}
+
+// Wait until the phase of parity par of a local mbarrier has completed
+// (acquire at cluster scope: the stores that completed it are visible).
+// Gives up after about a second (recording GN_ETIMEOUT), or soon after the
+// status word turns bad; returns whether the phase completed.
+__device__ __forceinline__ bool mb_wait(uint64_t *bar, uint32_t par, int32_t *status) {
+  const uint32_t a = smem_u32(bar);
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; it++) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(par)
+        : "memory");
+    if (done) return true;
+    if ((it & 15) == 15 && *(volatile int32_t *)status != GN_OK) return false;
+    if (clock64() - t0 > MF_WAIT_CYCLES) {
+      atomicCAS(status, GN_OK, GN_ETIMEOUT);
+      return false;
     }
   }
 }
 
-// Exact sum over the cluster of NV values of N limbs held by every thread:
-// each warp adds its lanes, writes the warp total to its slot in this CTA's
-// sSlot ([MF_WARPS][NV]), one cluster barrier, then warp 0 of every CTA adds
-// the MF_C x MF_WARPS slots.  On return all lanes of warp 0 hold the totals
-// in v.  *sOk = okv is this CTA's flag; the return value (valid in warp 0) is
-// the AND over the cluster.  Every thread of every CTA must call it, and two
-// calls with the same sSlot must be separated by another cluster barrier.
+__device__ __forceinline__ bool status_ok(const int32_t *status) {
+  return *(volatile const int32_t *)status == GN_OK;
+}
+
+// One reduction site: two slot buffers and two mbarriers, used alternately.
+// Use u writes buffer u & 1 and completes phase (u >> 1) & 1 of its
+// mbarrier.  A CTA sends its part of use u + 2 only after use u + 1 is
+// complete, which needs every CTA's part of use u + 1, which every warp
+// sends after reading its buffer for use u: so a buffer is never written
+// while it is read, and an mbarrier never holds two uses at once.  Every CTA
+// of a cluster makes the same uses in the same order.
+struct MbSite {
+  uint64_t *bar;   // [2]
+  uint64_t *slot;  // [2][slots][words]
+  uint32_t use;
+};
+
+// Exact cluster-wide sum of NV values of N limbs held by the lanes of ONE
+// warp in every CTA (use u of the site): the warp adds its lanes and sends
+// the total to every CTA (slot [rank]); the same warp of every CTA adds the 8
+// slots.  On return all lanes of the calling warps hold the totals.  A wait
+// that gives up leaves them undefined and the status word bad.
 template <int N, int NV>
-__device__ int cluster_sum(fx<N> (&v)[NV], fx<N> *sSlot, int *sOk, int okv, cg::cluster_group &cl) {
-  static_assert(MF_C * MF_WARPS == 64, "two slots per lane");
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u, int rank,
+                                 int32_t *status) {
+  constexpr int SW = N * NV;  // words per slot
+  const int lane = threadIdx.x & 31;
+  const uint32_t b = u & 1, par = (u >> 1) & 1;
+  uint64_t *bar = site.bar + b;
+  uint64_t *sl = site.slot + (size_t)b * MF_C * SW;
+  const bool live = status_ok(status);
+  if (lane == 0 && live) mb_expect(bar, MF_C * SW * 8);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
     for (int q = 0; q < NV; q++) {
-      fx<N> u;
+      fx<N> t;
 #pragma unroll
-      for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
-      v[q] = ix_add<N>(v[q], u);
+      for (int w = 0; w < N; w++) t.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
+      v[q] = ix_add<N>(v[q], t);
     }
-  if (lane == 0)
+  if (lane < MF_C && live) {
+    const uint32_t ra = cl_mapa(smem_u32(sl + (size_t)rank * SW), lane);
+    const uint32_t rb = cl_mapa(smem_u32(bar), lane);
 #pragma unroll
-    for (int q = 0; q < NV; q++) sSlot[warp * NV + q] = v[q];
-  if (threadIdx.x == 0) *sOk = okv;
-  cl.sync();
-  int all = 1;
-  if (warp == 0) {
-    const int e0 = lane, e1 = lane + 32;
-    const fx<N> *p0 = cl.map_shared_rank(sSlot, e0 / MF_WARPS) + (e0 % MF_WARPS) * NV;
-    const fx<N> *p1 = cl.map_shared_rank(sSlot, e1 / MF_WARPS) + (e1 % MF_WARPS) * NV;
+    for (int q = 0; q < NV; q++)
 #pragma unroll
-    for (int q = 0; q < NV; q++) v[q] = ix_add<N>(p0[q], p1[q]);
-    int okr = (lane < MF_C) ? *cl.map_shared_rank(sOk, lane) : 1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-      for (int q = 0; q < NV; q++) {
-        fx<N> u;
-#pragma unroll
-        for (int w = 0; w < N; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
-        v[q] = ix_add<N>(v[q], u);
-      }
-    all = __all_sync(0xffffffffu, okr);
+      for (int w = 0; w < N; w++) st_async8(ra + 8 * (q * N + w), v[q].w[w], rb);
   }
-  return all;
+  mb_wait(bar, par, status);
+#pragma unroll
+  for (int q = 0; q < NV; q++) {
+#pragma unroll
+    for (int w = 0; w < N; w++) v[q].w[w] = (lane < MF_C) ? sl[(size_t)lane * SW + q * N + w] : 0;
+  }
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1)
+#pragma unroll
+    for (int q = 0; q < NV; q++) {
+      fx<N> t;
+#pragma unroll
+      for (int w = 0; w < N; w++) t.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
+      v[q] = ix_add<N>(v[q], t);
+    }
+#pragma unroll
+  for (int q = 0; q < NV; q++)
+#pragma unroll
+    for (int w = 0; w < N; w++) v[q].w[w] = __shfl_sync(0xffffffffu, v[q].w[w], 0);
 }
+
+// Columns per ownership block: column j belongs to cluster (j / MF_B) mod G,
+// so the pivot chain stays inside one cluster for MF_B - 1 of every MF_B
+// columns.
+constexpr int MF_B = 4;
+
+// shared-memory layout of k_mgs_int, identical on host and device
+template <int L>
+struct MiLayout {
+  static constexpr int K = L;
+  static constexpr int SW_PIV = 2 * K + 1;  // norm: 2K+1 limbs
+  static constexpr int SW_DOT = 2 * (K + 1);  // a dot: re, im of K+1 limbs
+  size_t oS, oTb, oN0, oN0p, oR, oQ, oBar, oPiv, oLa, oBulk, oA, bytes;
+  __host__ __device__ MiLayout(int maxown, int ms, bool cols) {
+    size_t o = 0;
+    auto take = [&](size_t b) {
+      size_t at = o;
+      o += (b + 15) & ~(size_t)15;
+      return at;
+    };
+    const size_t msr = ms > 0 ? ms : 1;
+    oS = take(sizeof(int) * maxown);                   // column exponents s_j
+    oTb = take(sizeof(int) * maxown);                  // rank-test bit lengths
+    oN0 = take(sizeof(double) * maxown);               // original norms
+    oN0p = take(sizeof(double) * maxown);              // this CTA's part of them
+    oR = take(sizeof(fx<K>) * 2 * maxown);             // r_kj mantissas of a bulk step
+    oQ = take(sizeof(fx<K>) * 2 * msr);                // a pivot slice read from global memory
+    oBar = take(sizeof(uint64_t) * 6);                 // mbarriers: 3 sites x 2
+    oPiv = take(sizeof(uint64_t) * 2 * MF_C * SW_PIV);
+    oLa = take(sizeof(uint64_t) * 2 * MF_B * MF_C * SW_DOT);
+    oBulk = take(sizeof(uint64_t) * 2 * (size_t)maxown * MF_C * SW_DOT);
+    oA = take(cols ? sizeof(fx<K>) * 2 * msr * maxown : 0);  // the CTA's rows of its columns
+    bytes = (o + 255) & ~(size_t)255;
+  }
+};
 
 template <int L>
 __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   constexpr int K = L;          // limbs per real mantissa
   constexpr int W = 2 * L;      // doubles (= 64-bit words) per complex entry
   constexpr int S = 64 * K - 2; // scale of the pivot columns Q
+  constexpr int B = MF_B;
+  constexpr int SWD = MiLayout<L>::SW_DOT;
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -128,44 +193,56 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int m = a.m, ncols = a.ncols;
   const int ms = (m + MF_C - 1) / MF_C;
-  const int i0 = min(m, rank * ms), i1 = min(m, i0 + ms);
-  const int no = (g < ncols) ? (ncols - g + G - 1) / G : 0;
+  const int i0 = min(m, rank * ms), i1 = min(m, i0 + ms), nr = i1 - i0;
 
-  // shared memory
-  int *sS = (int *)smem;                                   // [maxown] column exponents s_j
-  int *sTb = sS + a.maxown;                                // [maxown] rank-test bit lengths
-  double *sN0 = (double *)(smem + 16 * ((a.maxown * 8 + 15) / 16));  // [maxown]
-  double *sN0p = sN0 + a.maxown;                           // [maxown]
-  fx<K + 1> *sDot = (fx<K + 1> *)(sN0p + a.maxown);        // [2][maxown][2] bulk partials
-  fx<K + 1> *sCritD = sDot + 4 * a.maxown;                 // [MF_WARPS][2] lookahead dot slots
-  fx<2 * K + 1> *sCritT = (fx<2 * K + 1> *)(sCritD + 2 * MF_WARPS);  // [MF_WARPS] norm slots
-  fx<K> *sR = (fx<K> *)(sCritT + MF_WARPS);                // [maxown + 1][2] r_kj mantissas
-  fx<K> *sQ = sR + 2 * (a.maxown + 1);                     // [ms][2] pivot slice
-  // wait results read by the cluster: [0,1] bulk step by parity, [2,3]
-  // lookahead step by parity, [4] the pivot's (always 1)
-  int *sOk = (int *)(sQ + 2 * (ms > 0 ? ms : 1));
-  int *sAll = sOk + 5;                                     // cluster decision broadcast
-  int *sB = sOk + 6;                                       // b_j of the pivot
-  int *sAccept = sOk + 7;
-  fx<K> *sZ = (fx<K> *)(sOk + 8);                          // normalisation multiplier
-  fx<K> *sTT = sZ + 1;                                     // t of the pivot (fraction)
+  // block-cyclic ownership: global column j <-> (owner, local index)
+  auto owner = [&](int j) { return (j / B) % G; };
+  auto lcol = [&](int j) { return ((j / B) / G) * B + (j % B); };
+  auto gcol = [&](int c) { return ((c / B) * G + g) * B + (c % B); };
+  const int nblk = (ncols + B - 1) / B;
+  int no = (g < nblk) ? ((nblk - g + G - 1) / G) * B : 0;  // my columns
+  if (no > 0 && owner(ncols - 1) == g) no -= nblk * B - ncols;
+  const int jlast = no > 0 ? gcol(no - 1) : -1;
+
+  const MiLayout<L> lay(a.maxown, ms, a.smem_cols != 0);
+  int *sS = (int *)(smem + lay.oS);
+  int *sTb = (int *)(smem + lay.oTb);
+  double *sN0 = (double *)(smem + lay.oN0);
+  double *sN0p = (double *)(smem + lay.oN0p);
+  fx<K> *sR = (fx<K> *)(smem + lay.oR);  // [maxown][2], by local column
+  fx<K> *sQ = (fx<K> *)(smem + lay.oQ);  // [ms][2]
+  fx<K> *sA = (fx<K> *)(smem + lay.oA);  // [maxown][ms][2]
+  uint64_t *bars = (uint64_t *)(smem + lay.oBar);
+  MbSite piv{bars + 0, (uint64_t *)(smem + lay.oPiv), 0};
+  MbSite la{bars + 2, (uint64_t *)(smem + lay.oLa), 0};
+  MbSite bulk{bars + 4, (uint64_t *)(smem + lay.oBulk), 0};
   bool ok = true;
 
-  auto col = [&](int j) { return (fx<K> *)(a.A + (int64_t)j * a.lda * W); };
+  if (tid == 0) {
+    for (int q = 0; q < 6; q++) mb_init(bars + q);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
 
-  // original column norms (double), exponents, conversion to mantissas in place
+  // this CTA's rows of global column j (the publication slot of pivots)
+  auto pubp = [&](int j) { return (fx<K> *)(a.A + ((int64_t)j * a.lda + i0) * W); };
+  // this CTA's rows of local column c: entry (i0 + r, part) at [2 r + part]
+  auto colp = [&](int c) {
+    return a.smem_cols ? sA + (size_t)c * ms * 2 : pubp(gcol(c));
+  };
+
+  // original column norms (double), exponents, conversion to mantissas
   for (int c = warp; c < no; c += MF_WARPS) {
-    const double *cp = a.A + (int64_t)(g + G * c) * a.lda * W;
+    const double *cp = a.A + ((int64_t)gcol(c) * a.lda + i0) * W;
     double s = 0.0;
-    for (int i = i0 + lane; i < i1; i += 32) {
-      double re = cp[(int64_t)i * W], im = cp[(int64_t)i * W + L];
+    for (int r = lane; r < nr; r += 32) {
+      double re = cp[(int64_t)r * W], im = cp[(int64_t)r * W + L];
       s = fma(re, re, fma(im, im, s));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) sN0p[c] = s;
   }
-  cl.sync();
+  cl.sync();  // also publishes the mbarrier initialisation to the cluster
   for (int c = tid; c < no; c += MF_THREADS) {
     double t = 0.0;
     for (int r = 0; r < MF_C; r++) t += cl.map_shared_rank(sN0p, r)[c];
@@ -177,16 +254,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     // on bit lengths: reject when bitlen(T) <= 2 (floor(log2 ||a_j^0||) + 8 - 50L - s_j) + 1
     sTb[c] = 2 * (fx_exponent_of(n0) - 1 + 8 - 50 * L - sj) + 1;
     if (rank == 0) {
-      a.nrm0[g + G * c] = n0;
-      a.nrm0[ncols + g + G * c] = (double)sj;
+      a.nrm0[gcol(c)] = n0;
+      a.nrm0[ncols + gcol(c)] = (double)sj;
     }
   }
   __syncthreads();
   for (int c = warp; c < no; c += MF_WARPS) {
-    double *cp = a.A + (int64_t)(g + G * c) * a.lda * W;
+    const double *cp = a.A + ((int64_t)gcol(c) * a.lda + i0) * W;
+    fx<K> *d = colp(c);
     const int F = -sS[c];
-    for (int i = i0 + lane; i < i1; i += 32) {
-      double *e = cp + (int64_t)i * W;
+    for (int r = lane; r < nr; r += 32) {
+      const double *e = cp + (int64_t)r * W;
       fx<K> re, im;
       fx_zero<K>(re);
       fx_zero<K>(im);
@@ -195,35 +273,39 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         ok &= fx_add_double<K>(re, e[l], F);
         ok &= fx_add_double<K>(im, e[L + l], F);
       }
-      fx<K> *d = (fx<K> *)e;
-      d[0] = re;
-      d[1] = im;
+      d[2 * r] = re;
+      d[2 * r + 1] = im;
     }
   }
   __syncthreads();
 
-  // pivot j: norm (exact), 1/||a_j|| by integer Newton, rank test,
-  // normalisation, publication; the R diagonal and 1/r_jj limbs afterwards
-  auto pivot = [&](int j, int c) {
-    fx<K> *aj = col(j);
+  // Pivot j by the one warp of each CTA that owns local column lcol(j): exact
+  // norm, cluster sum, 1/||a_j|| by integer Newton in lane 0, rank test,
+  // normalisation (into the CTA's column and the publication slot),
+  // release of the flag; the R diagonal and 1/r_jj afterwards.
+  auto pivot = [&](int j, uint32_t u) {
+    const int c = lcol(j);
+    fx<K> *aj = colp(c);
     const int sj = sS[c];
     fx<2 * K + 1> t[1];
     fx_zero<2 * K + 1>(t[0]);
-    for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
-      const int i = i0 + (e >> 1), part = e & 1;
-      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * i + part]));
+    for (int r = lane; r < nr; r += 32) {
+      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * r]));
+      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * r + 1]));
     }
-    cluster_sum<2 * K + 1, 1>(t, sCritT, sOk + 4, 1, cl);
+    warp_cluster_sum<2 * K + 1, 1>(t, piv, u, rank, a.status);
     ux<K> Y;
-    int bl = 0, b = 0;
-    if (tid == 0) {
+    fx<K> Z;
+    ux<K> tt;
+    int bl = 0, b = 0, accept = 0;
+    fx_zero<K>(Z);
+    if (lane == 0) {
       const fx<2 * K + 1> T = t[0];
       bl = ix_bitlen<2 * K + 1>(T);
       b = (bl + 1) >> 1;  // sqrt(T) < 2^b
-      int accept = (bl > 0) && (j == ncols - 1 || bl > sTb[c]);
+      accept = (bl > 0) && (j == ncols - 1 || bl > sTb[c]);
       if (!accept && j < ncols - 1) atomicCAS(a.status, GN_OK, GN_ESINGULAR);
       // t = T / 2^(2b) in [1/4, 1) as K limbs of fraction
-      ux<K> tt;
       {
         fx<2 * K + 1> sh;
         const int d = 2 * b - 64 * K;
@@ -236,30 +318,25 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
 #pragma unroll
         for (int w = 0; w < K; w++) tt.w[w] = sh.w[w];
       }
-      fx<K> Z;
-      fx_zero<K>(Z);
       if (accept) {
         Y = ix_rsqrt_frac<K>(tt);  // 2^S / sqrt(t)
 #pragma unroll
         for (int w = 0; w < K; w++) Z.w[w] = (Y.w[w] >> 1) | ((w + 1 < K) ? (Y.w[w + 1] << 63) : 0);
       }
-      *sZ = Z;
-      *sB = b;
-      *sAccept = accept;
-#pragma unroll
-      for (int w = 0; w < K; w++) sTT->w[w] = tt.w[w];
     }
-    __syncthreads();
     if (j < ncols - 1) {
-      if (*sAccept) {
-        const fx<K> Z = *sZ;
-        const int sh = *sB - 1;
+#pragma unroll
+      for (int w = 0; w < K; w++) Z.w[w] = __shfl_sync(0xffffffffu, Z.w[w], 0);
+      b = __shfl_sync(0xffffffffu, b, 0);
+      accept = __shfl_sync(0xffffffffu, accept, 0);
+      if (accept) {
+        const int sh = b - 1;
         uint64_t nz;
         const ux<K> uz = ix_abs<K>(Z, nz);
-        for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
-          const int i = i0 + (e >> 1), part = e & 1;
+        fx<K> *pj = pubp(j);
+        for (int e = lane; e < 2 * nr; e += 32) {
           uint64_t na;
-          ux<K> ua = ix_abs<K>(aj[2 * i + part], na);
+          ux<K> ua = ix_abs<K>(aj[e], na);
           ux<2 * K> p = ix_umul<K>(ua, uz);
           fx<2 * K> pf;
 #pragma unroll
@@ -269,253 +346,316 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
 #pragma unroll
           for (int w = 0; w < K; w++) q.w[w] = pf.w[w];
           ix_cneg<K>(q, na);
-          aj[2 * i + part] = q;
+          aj[e] = q;
+          if (a.smem_cols) pj[e] = q;
         }
       }
-      __syncthreads();
-      if (tid == 0) st_release(a.flags + (size_t)j * MF_C + rank, *sAccept ? 1u : 2u);
+      __syncwarp();  // the warp's stores of q_j are ordered before lane 0's release
+      if (lane == 0) st_release(a.flags + (size_t)j * MF_C + rank, accept ? 1u : 2u);
     }
-    // off the critical path: r_jj, 1/r_jj as limbs, and the pivot's mantissa for back substitution
-    if (tid == 0 && rank == 0) {
-      cx<L> rc = c_zero<L>();
-      if (bl > 0) {
-        ux<K> tt;
+    // for back substitution and the R output: 1/r_jj = Z 2^e, and t and b in
+    // the diagonal slot of R (k_mgs_r_out forms r_jj and 1/r_jj from them)
+    if (lane == 0 && rank == 0) {
+      if (accept && j < ncols - 1) {
+        double *zs = a.Zs + (size_t)j * (K + 1);
 #pragma unroll
-        for (int w = 0; w < K; w++) tt.w[w] = sTT->w[w];
-        if (!*sAccept) Y = ix_rsqrt_frac<K>(tt);
-        // sqrt(t) = t y: (tt Y) / 2^(64K), scale 2^S
-        ux<2 * K> ty = ix_umul<K>(tt, Y);
-        fx<K> M;
-#pragma unroll
-        for (int w = 0; w < K; w++) M.w[w] = ty.w[K + w];
-        fx_to_cascade<K, L>(M, S - b - sj, rc.re);  // r_jj = sqrt(t) 2^(b + s_j)
-        if (*sAccept && j < ncols - 1) {
-          fx<K> Yf;
-#pragma unroll
-          for (int w = 0; w < K; w++) Yf.w[w] = Y.w[w];
-          double ri[L];
-          fx_to_cascade<K, L>(Yf, S + b + sj, ri);  // 1/r_jj = y 2^-(b + s_j)
-#pragma unroll
-          for (int l = 0; l < L; l++) a.rinv[(int64_t)j * L + l] = ri[l];
-          if (a.Zs) {
-            double *zs = a.Zs + (size_t)j * (K + 1);
-            const fx<K> Z = *sZ;
-#pragma unroll
-            for (int w = 0; w < K; w++) ((uint64_t *)zs)[w] = Z.w[w];
-            zs[K] = (double)(-(b + 64 * K - 3) - sj);  // 1/r_jj = Z 2^this
-          }
-        }
+        for (int w = 0; w < K; w++) ((uint64_t *)zs)[w] = Z.w[w];
+        zs[K] = (double)(-(b + 64 * K - 3) - sj);  // 1/r_jj = Z 2^this
       }
-      c_store<L>(a.R + ((int64_t)j * a.ldr + j) * W, rc);
+      uint64_t *rd = (uint64_t *)(a.R + ((int64_t)j * a.ldr + j) * W);
+#pragma unroll
+      for (int w = 0; w < K; w++) rd[w] = (bl > 0) ? tt.w[w] : 0;
+      rd[K] = (uint64_t)b;
     }
   };
 
-  if (g == 0 && no > 0) pivot(0, 0);
+  // r_kj = q_k^H a_j as K-limb mantissas at the scale of column j
+  // (|r_kj| <= ||a_j^0||, so they fit; k_mgs_r_out converts them)
+  auto out_r = [&](int k, int c, const fx<K + 1> &tr, const fx<K + 1> &ti) {
+    fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)gcol(c) * a.ldr + k) * W);
+    rm[0] = ix_narrow<K>(tr);
+    rm[1] = ix_narrow<K>(ti);
+  };
 
-  for (int k = 0; k < ncols - 1; k++) {
-    const int cstart = (k + 1 > g) ? (k + 1 - g + G - 1) / G : 0;
-    if (cstart >= no) break;
-    // wait for the rows of q_k that this CTA needs; the cluster compares
-    // notes at the step's first barrier
-    int okv = 1;
-    if (tid == 0) {
-      const uint32_t *f = a.flags + (size_t)k * MF_C + rank;
-      const long long t0 = clock64();
-      uint32_t v;
-      for (;;) {
-        v = ld_acquire(f);
-        if (v) break;
-        if (*(volatile int32_t *)a.status != GN_OK) {
-          v = 2;
-          break;
-        }
-        if (clock64() - t0 > MF_WAIT_CYCLES) {
-          atomicCAS(a.status, GN_OK, GN_ETIMEOUT);
-          v = 2;
-          break;
-        }
-        __nanosleep(32);
+  // conj(q)^T a over this CTA's rows for one column, by one warp; lanes over rows
+  auto warp_dot = [&](const fx<K> *q, const fx<K> *aj, fx<K + 1> &dr, fx<K + 1> &di) {
+    fx_zero<K + 1>(dr);
+    fx_zero<K + 1>(di);
+    for (int r = lane; r < nr; r += 32) {
+      const fx<K> qr = q[2 * r], qi = q[2 * r + 1];
+      const fx<K> ar = aj[2 * r], ai = aj[2 * r + 1];
+      dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qr, ar));
+      dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qi, ai));
+      di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
+      di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      fx<K + 1> u, v;
+#pragma unroll
+      for (int w = 0; w < K + 1; w++) {
+        u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
+        v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
       }
-      okv = (v == 1);
+      dr = ix_add<K + 1>(dr, u);
+      di = ix_add<K + 1>(di, v);
+    }
+  };
+
+  // a_j <- a_j - r q over this CTA's rows, by one warp
+  auto warp_axpy = [&](const fx<K> *q, fx<K> *aj, const fx<K> &rr, const fx<K> &ri) {
+    for (int r = lane; r < nr; r += 32) {
+      const fx<K> qr = q[2 * r], qi = q[2 * r + 1];
+      fx<K + 1> xr = ix_widen<K, K + 1>(aj[2 * r]);
+      fx<K + 1> xi = ix_widen<K, K + 1>(aj[2 * r + 1]);
+      xr = ix_sub<K + 1>(xr, ix_mul_shift<K>(rr, qr));
+      xr = ix_add<K + 1>(xr, ix_mul_shift<K>(ri, qi));
+      xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(rr, qi));
+      xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(ri, qr));
+      aj[2 * r] = ix_narrow<K>(xr);
+      aj[2 * r + 1] = ix_narrow<K>(xi);
+    }
+  };
+
+  // send this warp's dot to slot [t][rank] of every CTA of the cluster
+  auto send_dot = [&](uint64_t *sl, uint64_t *bar, int t, const fx<K + 1> &dr, const fx<K + 1> &di,
+                      bool live) {
+    if (lane < MF_C && live) {
+      const uint32_t ra = cl_mapa(smem_u32(sl + ((size_t)t * MF_C + rank) * SWD), lane);
+      const uint32_t rb = cl_mapa(smem_u32(bar), lane);
+#pragma unroll
+      for (int w = 0; w < K + 1; w++) {
+        st_async8(ra + 8 * w, dr.w[w], rb);
+        st_async8(ra + 8 * (K + 1 + w), di.w[w], rb);
+      }
+    }
+  };
+
+  // Apply q_k (this CTA's rows at q) to the local columns [cf, no): dots by
+  // warps, totals through the bulk site, axpys.  Every thread calls it.
+  auto bulk_apply = [&](int k, const fx<K> *q, int cf) {
+    const int nb = no - cf;
+    if (nb <= 0) return;
+    const uint32_t u = bulk.use++;
+    const uint32_t bb = u & 1, par = (u >> 1) & 1;
+    uint64_t *bar = bulk.bar + bb;
+    uint64_t *sl = bulk.slot + (size_t)bb * a.maxown * MF_C * SWD;
+    const bool live = status_ok(a.status);
+    if (tid == 0 && live) mb_expect(bar, (uint32_t)(nb * MF_C * SWD * 8));
+    for (int cc = warp; cc < nb; cc += MF_WARPS) {
+      fx<K + 1> dr, di;
+      warp_dot(q, colp(cf + cc), dr, di);
+      send_dot(sl, bar, cc, dr, di, live);
+    }
+    mb_wait(bar, par, a.status);
+    for (int cc = tid; cc < nb; cc += MF_THREADS) {
+      fx<K + 1> tr, ti;
+      fx_zero<K + 1>(tr);
+      fx_zero<K + 1>(ti);
+      for (int r = 0; r < MF_C; r++) {
+        const uint64_t *p = sl + ((size_t)cc * MF_C + r) * SWD;
+        fx<K + 1> x, y;
+#pragma unroll
+        for (int w = 0; w < K + 1; w++) {
+          x.w[w] = p[w];
+          y.w[w] = p[K + 1 + w];
+        }
+        tr = ix_add<K + 1>(tr, x);
+        ti = ix_add<K + 1>(ti, y);
+      }
+      sR[2 * cc] = ix_narrow<K>(tr);
+      sR[2 * cc + 1] = ix_narrow<K>(ti);
+      if (rank == 0) out_r(k, cf + cc, tr, ti);
     }
     __syncthreads();
-    const fx<K> *qk = col(k);
-    for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
-      const int i = i0 + (e >> 1), part = e & 1;
+    for (int cc = warp; cc < nb; cc += MF_WARPS) warp_axpy(q, colp(cf + cc), sR[2 * cc], sR[2 * cc + 1]);
+    __syncthreads();  // sR, sQ and the slots are free for the next use
+  };
+
+  // this CTA's rows of q_k from the publication slot into sQ (after its flag)
+  auto load_q = [&](int k) {
+    const fx<K> *qk = pubp(k);
+    for (int e = tid; e < 2 * nr; e += MF_THREADS) {
       fx<K> v;
 #pragma unroll
-      for (int w = 0; w < K; w++) v.w[w] = __ldcg(&qk[2 * i + part].w[w]);
-      sQ[2 * (i - i0) + part] = v;
+      for (int w = 0; w < K; w++) v.w[w] = __ldcg(&qk[e].w[w]);
+      sQ[e] = v;
     }
     __syncthreads();
+  };
 
-    int cb = cstart;
-    const int j1 = k + 1;
-    int allok = 1;
-    if (j1 % G == g) {
-      // lookahead column: 2 threads per row (real part, imaginary part)
-      const int c = (j1 - g) / G;
-      fx<K> *aj = col(j1);
-      const int sj = sS[c];
-      fx<K + 1> d2[2];
-      fx_zero<K + 1>(d2[0]);
-      fx_zero<K + 1>(d2[1]);
-      for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
-        const int i = i0 + (e >> 1), part = e & 1;
-        const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
-        const fx<K> ar = aj[2 * i], ai = aj[2 * i + 1];
-        if (part == 0) {  // Re conj(q) a = qr ar + qi ai
-          d2[0] = ix_add<K + 1>(d2[0], ix_mul_shift<K>(qr, ar));
-          d2[0] = ix_add<K + 1>(d2[0], ix_mul_shift<K>(qi, ai));
-        } else {  // Im conj(q) a = qr ai - qi ar
-          d2[1] = ix_add<K + 1>(d2[1], ix_mul_shift<K>(qr, ai));
-          d2[1] = ix_sub<K + 1>(d2[1], ix_mul_shift<K>(qi, ar));
+  if (owner(0) == g && no > 0) {
+    const uint32_t u = piv.use++;
+    if (warp == 0) pivot(0, u);
+    __syncthreads();
+  }
+
+  int kp = 0;  // first q not yet applied to the columns outside the current block
+  int cf = 0;  // first local column with global index > k
+  for (int k = 0; k < ncols - 1; k++) {
+    if (k >= jlast) break;
+    while (cf < no && gcol(cf) <= k) cf++;
+    const bool lak = owner(k + 1) == g;  // this cluster takes the pivot chain
+    // columns outside the block get the pending q's first (MGS order), also
+    // before a new block of this cluster starts
+    if (!lak || (k + 1) % B == 0) {
+      for (int kk = kp; kk < k; kk++) {
+        if (owner(kk) == g) {
+          bulk_apply(kk, colp(lcol(kk)), cf);
+        } else {
+          load_q(kk);
+          bulk_apply(kk, sQ, cf);
         }
       }
-      allok = cluster_sum<K + 1, 2>(d2, sCritD, sOk + 2 + (k & 1), okv, cl);
-      if (tid == 0) {
-        *sAll = allok;
-        sR[2 * a.maxown] = ix_narrow<K>(d2[0]);
-        sR[2 * a.maxown + 1] = ix_narrow<K>(d2[1]);
-      }
-      __syncthreads();
-      allok = *sAll;
-      if (!allok) break;
-      {
-        const fx<K> rr = sR[2 * a.maxown], ri = sR[2 * a.maxown + 1];
-        for (int e = tid; e < 2 * (i1 - i0); e += MF_THREADS) {
-          const int i = i0 + (e >> 1), part = e & 1;
-          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
-          fx<K + 1> x = ix_widen<K, K + 1>(aj[2 * i + part]);
-          if (part == 0) {  // Re(a - r q) = ar - rr qr + ri qi
-            x = ix_sub<K + 1>(x, ix_mul_shift<K>(rr, qr));
-            x = ix_add<K + 1>(x, ix_mul_shift<K>(ri, qi));
-          } else {  // Im(a - r q) = ai - rr qi - ri qr
-            x = ix_sub<K + 1>(x, ix_mul_shift<K>(rr, qi));
-            x = ix_sub<K + 1>(x, ix_mul_shift<K>(ri, qr));
-          }
-          aj[2 * i + part] = ix_narrow<K>(x);
-        }
-      }
-      __syncthreads();
-      pivot(j1, c);
-      if (tid == 0 && rank == 0) {  // r_kj of the lookahead column, after the publication
-        const fx<K> rr = sR[2 * a.maxown], ri = sR[2 * a.maxown + 1];
-        if (a.Rm) {
-          fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)j1 * a.ldr + k) * W);
-          rm[0] = rr;
-          rm[1] = ri;
-        }
-        cx<L> rk;
-        fx_to_cascade<K, L>(rr, -sj, rk.re);
-        fx_to_cascade<K, L>(ri, -sj, rk.im);
-        c_store<L>(a.R + ((int64_t)j1 * a.ldr + k) * W, rk);
-      }
-      cb = c + 1;
+      kp = k;
     }
-    const int nb = no - cb;
-    if (nb > 0) {
-      const int buf = k & 1;
-      for (int cc = warp; cc < nb; cc += MF_WARPS) {
-        const int c = cb + cc;
-        const fx<K> *aj = col(g + G * c);
+    // q_k: this cluster's own, or published by its owner
+    const fx<K> *q;
+    if (owner(k) == g) {
+      q = colp(lcol(k));
+      // stop after a singular pivot of this cluster (decided by thread 0 for all)
+      if (__syncthreads_or(tid == 0 && !status_ok(a.status))) break;
+    } else {
+      int okv = 1;
+      if (tid == 0) {
+        const uint32_t *f = a.flags + (size_t)k * MF_C + rank;
+        const long long t0 = clock64();
+        uint32_t v;
+        for (;;) {
+          v = ld_acquire(f);
+          if (v) break;
+          if (!status_ok(a.status)) {
+            v = 2;
+            break;
+          }
+          if (clock64() - t0 > MF_WAIT_CYCLES) {
+            atomicCAS(a.status, GN_OK, GN_ETIMEOUT);
+            v = 2;
+            break;
+          }
+          __nanosleep(32);
+        }
+        okv = (v == 1) && status_ok(a.status);
+      }
+      // the one place a CTA leaves the loop early: uniform over the CTA; the
+      // other CTAs of the cluster then find the status bad in their next wait
+      if (__syncthreads_or(tid == 0 && !okv)) break;
+      load_q(k);
+      q = sQ;
+    }
+    if (lak) {
+      // the block's columns after k, warp (j mod B) each: dot, cluster sum, axpy;
+      // then the pivot k+1 by its warp, which publishes q_{k+1}
+      const int j1 = k + 1, jend = min(((k + 1) / B + 1) * B, ncols), nla = jend - j1;
+      const uint32_t u = la.use++;
+      const uint32_t bb = u & 1, par = (u >> 1) & 1;
+      uint64_t *bar = la.bar + bb;
+      uint64_t *sl = la.slot + (size_t)bb * B * MF_C * SWD;
+      const bool live = status_ok(a.status);
+      if (tid == 0 && live) mb_expect(bar, (uint32_t)(nla * MF_C * SWD * 8));
+      const int t = warp - (j1 % B);  // this warp's column j1 + t
+      if (warp < B && t >= 0 && t < nla) {
+        const int c = lcol(j1 + t);
+        fx<K> *aj = colp(c);
         fx<K + 1> dr, di;
-        fx_zero<K + 1>(dr);
-        fx_zero<K + 1>(di);
-        for (int i = i0 + lane; i < i1; i += 32) {
-          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
-          const fx<K> ar = aj[2 * i], ai = aj[2 * i + 1];
-          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qr, ar));
-          dr = ix_add<K + 1>(dr, ix_mul_shift<K>(qi, ai));
-          di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
-          di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
+        warp_dot(q, aj, dr, di);
+        send_dot(sl, bar, t, dr, di, live);
+        mb_wait(bar, par, a.status);
+        fx<K + 1> v[2];
+#pragma unroll
+        for (int w = 0; w < K + 1; w++) {
+          v[0].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + w] : 0;
+          v[1].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + K + 1 + w] : 0;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          fx<K + 1> u, v;
+        for (int o = 4; o > 0; o >>= 1) {
+          fx<K + 1> x, y;
 #pragma unroll
           for (int w = 0; w < K + 1; w++) {
-            u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
-            v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
+            x.w[w] = __shfl_xor_sync(0xffffffffu, v[0].w[w], o);
+            y.w[w] = __shfl_xor_sync(0xffffffffu, v[1].w[w], o);
           }
-          dr = ix_add<K + 1>(dr, u);
-          di = ix_add<K + 1>(di, v);
+          v[0] = ix_add<K + 1>(v[0], x);
+          v[1] = ix_add<K + 1>(v[1], y);
         }
-        if (lane == 0) {
-          sDot[(buf * a.maxown + c) * 2] = dr;
-          sDot[(buf * a.maxown + c) * 2 + 1] = di;
+#pragma unroll
+        for (int w = 0; w < K + 1; w++) {
+          v[0].w[w] = __shfl_sync(0xffffffffu, v[0].w[w], 0);
+          v[1].w[w] = __shfl_sync(0xffffffffu, v[1].w[w], 0);
         }
-      }
-      if (tid == 0) sOk[buf] = (j1 % G == g) ? 1 : okv;  // lookahead already checked the wait
-      cl.sync();
-      if (warp == 0) {
-        int okr = (lane < MF_C) ? cl.map_shared_rank(sOk, lane)[buf] : 1;
-        okr = __all_sync(0xffffffffu, okr);
-        if (lane == 0) *sAll = okr;
-      }
-      for (int cc = tid; cc < nb; cc += MF_THREADS) {
-        const int c = cb + cc;
-        fx<K + 1> tr, ti;
-        fx_zero<K + 1>(tr);
-        fx_zero<K + 1>(ti);
-        for (int r = 0; r < MF_C; r++) {
-          const fx<K + 1> *p = cl.map_shared_rank(sDot, r) + (buf * a.maxown + c) * 2;
-          tr = ix_add<K + 1>(tr, p[0]);
-          ti = ix_add<K + 1>(ti, p[1]);
-        }
-        sR[2 * c] = ix_narrow<K>(tr);
-        sR[2 * c + 1] = ix_narrow<K>(ti);
-        if (rank == 0) {
-          if (a.Rm) {
-            fx<K> *rm = (fx<K> *)(a.Rm + ((int64_t)(g + G * c) * a.ldr + k) * W);
-            rm[0] = sR[2 * c];
-            rm[1] = sR[2 * c + 1];
-          }
-          cx<L> rk;
-          fx_to_cascade<K + 1, L>(tr, -sS[c], rk.re);
-          fx_to_cascade<K + 1, L>(ti, -sS[c], rk.im);
-          c_store<L>(a.R + ((int64_t)(g + G * c) * a.ldr + k) * W, rk);
+        warp_axpy(q, aj, ix_narrow<K>(v[0]), ix_narrow<K>(v[1]));
+        if (t > 0 && lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
+        if (t == 0) {
+          const uint32_t pu = piv.use;
+          pivot(j1, pu);
+          if (lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
         }
       }
-      __syncthreads();
-      if (!*sAll) break;
-      for (int cc = warp; cc < nb; cc += MF_WARPS) {
-        const int c = cb + cc;
-        fx<K> *aj = col(g + G * c);
-        const fx<K> rr = sR[2 * c], ri = sR[2 * c + 1];
-        for (int i = i0 + lane; i < i1; i += 32) {
-          const fx<K> qr = sQ[2 * (i - i0)], qi = sQ[2 * (i - i0) + 1];
-          fx<K + 1> xr = ix_widen<K, K + 1>(aj[2 * i]);
-          fx<K + 1> xi = ix_widen<K, K + 1>(aj[2 * i + 1]);
-          xr = ix_sub<K + 1>(xr, ix_mul_shift<K>(rr, qr));
-          xr = ix_add<K + 1>(xr, ix_mul_shift<K>(ri, qi));
-          xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(rr, qi));
-          xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(ri, qr));
-          aj[2 * i] = ix_narrow<K>(xr);
-          aj[2 * i + 1] = ix_narrow<K>(xi);
-        }
-      }
+      piv.use++;
+      __syncthreads();  // q_{k+1} and the block's columns are visible to every warp
+    } else {
+      bulk_apply(k, q, cf);
+      kp = k + 1;
     }
   }
   if (!ok) atomicCAS(a.status, GN_OK, GN_ENONFINITE);
+  // the residual column b - Q y back to global memory
+  if (a.smem_cols && no > 0 && owner(ncols - 1) == g && status_ok(a.status)) {
+    const fx<K> *src = colp(lcol(ncols - 1));
+    fx<K> *dst = pubp(ncols - 1);
+    for (int e = tid; e < 2 * nr; e += MF_THREADS) dst[e] = src[e];
+  }
+  // after a failure, asynchronous stores sent before it may still be in
+  // flight towards CTAs that no longer wait for them: let them land
+  if (!status_ok(a.status)) __nanosleep(20000);
   cl.sync();
 }
 
+// R from the mantissas k_mgs_int left: r_kj = Rm_kj 2^(s_j) above the
+// diagonal; on it, t and b of the pivot give r_jj = sqrt(t) 2^(b + s_j) and
+// 1/r_jj = (1/sqrt(t)) 2^-(b + s_j); zeros below.  One CTA per column.
 template <int L>
-struct MiLayout {
-  size_t bytes;
-  __host__ __device__ MiLayout(int maxown, int ms) {
-    constexpr int K = L;
-    size_t b = 16 * ((maxown * 8 + 15) / 16);
-    b += 16 * maxown;                                  // sN0, sN0p
-    b += sizeof(fx<K + 1>) * (4 * maxown + 2 * MF_WARPS);  // sDot, sCritD
-    b += sizeof(fx<2 * K + 1>) * MF_WARPS;             // sCritT
-    b += sizeof(fx<K>) * 2 * (maxown + 1);             // sR
-    b += sizeof(fx<K>) * 2 * (ms > 0 ? ms : 1);        // sQ
-    b += 32 + 2 * sizeof(fx<K>) + 64;                  // flags, Z, t, slack
-    bytes = (b + 255) & ~(size_t)255;
+__global__ void k_mgs_r_out(double *R, const double *Rm, int64_t ldr, int32_t ncols,
+                            const double *sexp, double *rinv, const int32_t *status) {
+  constexpr int K = L, W = 2 * L, S = 64 * K - 2;
+  if (*status != GN_OK) return;
+  const int j = blockIdx.x;
+  const int sj = (int)sexp[j];
+  double *col = R + (int64_t)j * ldr * W;
+  for (int k = threadIdx.x; k < ncols; k += blockDim.x) {
+    cx<L> z = c_zero<L>();
+    if (k < j) {
+      const fx<K> *rm = (const fx<K> *)(Rm + ((int64_t)j * ldr + k) * W);
+      fx_to_cascade<K, L>(rm[0], -sj, z.re);
+      fx_to_cascade<K, L>(rm[1], -sj, z.im);
+    } else if (k == j) {
+      const uint64_t *rd = (const uint64_t *)(col + (int64_t)j * W);
+      ux<K> tt;
+#pragma unroll
+      for (int w = 0; w < K; w++) tt.w[w] = rd[w];
+      const int b = (int)rd[K];
+      if (b > 0) {
+        const ux<K> Y = ix_rsqrt_frac<K>(tt);  // 2^S / sqrt(t)
+        // sqrt(t) = t y: (tt Y) / 2^(64K), scale 2^S
+        const ux<2 * K> ty = ix_umul<K>(tt, Y);
+        fx<K> M, Yf;
+#pragma unroll
+        for (int w = 0; w < K; w++) {
+          M.w[w] = ty.w[K + w];
+          Yf.w[w] = Y.w[w];
+        }
+        fx_to_cascade<K, L>(M, S - b - sj, z.re);  // r_jj = sqrt(t) 2^(b + s_j)
+        if (j < ncols - 1) {
+          double ri[L];
+          fx_to_cascade<K, L>(Yf, S + b + sj, ri);  // 1/r_jj = y 2^-(b + s_j)
+#pragma unroll
+          for (int l = 0; l < L; l++) rinv[(int64_t)j * L + l] = ri[l];
+        }
+      }
+    }
+    c_store<L>(col + (int64_t)k * W, z);
   }
-};
+}
 
 // Q (and the residual b - Q y) back from mantissas to L-limb cascades:
 // column j < n at scale 2^-(64K-2), the last column at 2^s_n.
