@@ -421,7 +421,7 @@ def breakdown(S, system, dev, flush, args):
                     "unit": "G IMAD/s", "frac": achieved / IMAD_PEAK_GINSTR,
                     "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2.07 GHz",
                     # ncu, one DD launch inside the Newton step (k_mgs_int_dd_gn256.md)
-                    "traffic": 2.50e6 if L == 2 else None,
+                    "traffic": 2.27e6 if L == 2 else None,
                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch",
                     "algorithmic_imad": work, "launch_ms": t_mgs,
                     "us_per_column": 1e3 * t_mgs / (system.n + 1),

@@ -77,6 +77,32 @@ __device__ __forceinline__ bool status_ok(const int32_t *status) {
   return *(volatile const int32_t *)status == GN_OK;
 }
 
+// arrival (release at CTA scope) on a local mbarrier
+__device__ __forceinline__ void mb_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warps 0 .. MF_CW-1 run the factorisation; warp MF_CW releases the pivot
+// flags (a release at GPU scope waits for the pivot's global stores, about
+// a microsecond, which must not sit on the pivot chain).  The compute warps
+// synchronise among themselves on named barrier 1.
+constexpr int MF_CW = MF_WARPS - 1;
+constexpr int MF_CT = MF_CW * 32;
+constexpr int MF_NPUB = 4;  // pivots handed to the publisher warp in flight
+
+__device__ __forceinline__ void cw_sync() { asm volatile("bar.sync 1, %0;" ::"n"(MF_CT) : "memory"); }
+
+__device__ __forceinline__ int cw_sync_or(int pred) {
+  int r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\tsetp.ne.s32 q, %1, 0;\n\t"
+      "bar.red.or.pred p, 1, %2, q;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(pred), "n"(MF_CT)
+      : "memory");
+  return r;
+}
+
 // One reduction site: two slot buffers and two mbarriers, used alternately.
 // Use u writes buffer u & 1 and completes phase (u >> 1) & 1 of its
 // mbarrier.  A CTA sends its part of use u + 2 only after use u + 1 is
@@ -103,8 +129,7 @@ __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u,
   const uint32_t b = u & 1, par = (u >> 1) & 1;
   uint64_t *bar = site.bar + b;
   uint64_t *sl = site.slot + (size_t)b * MF_C * SW;
-  const bool live = status_ok(status);
-  if (lane == 0 && live) mb_expect(bar, MF_C * SW * 8);
+  if (lane == 0) mb_expect(bar, MF_C * SW * 8);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -114,7 +139,7 @@ __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u,
       for (int w = 0; w < N; w++) t.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
       v[q] = ix_add<N>(v[q], t);
     }
-  if (lane < MF_C && live) {
+  if (lane < MF_C) {
     const uint32_t ra = cl_mapa(smem_u32(sl + (size_t)rank * SW), lane);
     const uint32_t rb = cl_mapa(smem_u32(bar), lane);
 #pragma unroll
@@ -154,7 +179,8 @@ struct MiLayout {
   static constexpr int K = L;
   static constexpr int SW_PIV = 2 * K + 1;  // norm: 2K+1 limbs
   static constexpr int SW_DOT = 2 * (K + 1);  // a dot: re, im of K+1 limbs
-  size_t oS, oTb, oN0, oN0p, oR, oQ, oBar, oPiv, oLa, oBulk, oA, bytes;
+  static constexpr int NBAR = 6 + 2 * MF_NPUB;  // 3 sites x 2, publication full/empty
+  size_t oS, oTb, oN0, oN0p, oR, oQ, oBar, oPub, oPiv, oLa, oBulk, oA, bytes;
   __host__ __device__ MiLayout(int maxown, int ms, bool cols) {
     size_t o = 0;
     auto take = [&](size_t b) {
@@ -169,7 +195,8 @@ struct MiLayout {
     oN0p = take(sizeof(double) * maxown);              // this CTA's part of them
     oR = take(sizeof(fx<K>) * 2 * maxown);             // r_kj mantissas of a bulk step
     oQ = take(sizeof(fx<K>) * 2 * msr);                // a pivot slice read from global memory
-    oBar = take(sizeof(uint64_t) * 6);                 // mbarriers: 3 sites x 2
+    oBar = take(sizeof(uint64_t) * NBAR);              // mbarriers
+    oPub = take(sizeof(int) * 2 * MF_NPUB);            // handed-off pivots: column, accepted
     oPiv = take(sizeof(uint64_t) * 2 * MF_C * SW_PIV);
     oLa = take(sizeof(uint64_t) * 2 * MF_B * MF_C * SW_DOT);
     oBulk = take(sizeof(uint64_t) * 2 * (size_t)maxown * MF_C * SW_DOT);
@@ -213,13 +240,15 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   fx<K> *sQ = (fx<K> *)(smem + lay.oQ);  // [ms][2]
   fx<K> *sA = (fx<K> *)(smem + lay.oA);  // [maxown][ms][2]
   uint64_t *bars = (uint64_t *)(smem + lay.oBar);
+  uint64_t *pubFull = bars + 6, *pubEmpty = bars + 6 + MF_NPUB;
+  int *sPubJ = (int *)(smem + lay.oPub), *sPubAcc = sPubJ + MF_NPUB;
   MbSite piv{bars + 0, (uint64_t *)(smem + lay.oPiv), 0};
   MbSite la{bars + 2, (uint64_t *)(smem + lay.oLa), 0};
   MbSite bulk{bars + 4, (uint64_t *)(smem + lay.oBulk), 0};
   bool ok = true;
 
   if (tid == 0) {
-    for (int q = 0; q < 6; q++) mb_init(bars + q);
+    for (int q = 0; q < MiLayout<L>::NBAR; q++) mb_init(bars + q);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
@@ -350,8 +379,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           if (a.smem_cols) pj[e] = q;
         }
       }
-      __syncwarp();  // the warp's stores of q_j are ordered before lane 0's release
-      if (lane == 0) st_release(a.flags + (size_t)j * MF_C + rank, accept ? 1u : 2u);
+      // hand q_j to the publisher warp: the warp's stores are ordered before
+      // lane 0's arrival (release), the publisher's flag release after it
+      __syncwarp();
+      if (lane == 0) {
+        const int pp = lcol(j), ps = pp % MF_NPUB;
+        if (mb_wait(pubEmpty + ps, ((pp / MF_NPUB) & 1) ^ 1, a.status)) {
+          sPubJ[ps] = j;
+          sPubAcc[ps] = accept;
+          mb_arrive(pubFull + ps);
+        }
+      }
     }
     // for back substitution and the R output: 1/r_jj = Z 2^e, and t and b in
     // the diagonal slot of R (k_mgs_r_out forms r_jj and 1/r_jj from them)
@@ -418,9 +456,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   };
 
   // send this warp's dot to slot [t][rank] of every CTA of the cluster
-  auto send_dot = [&](uint64_t *sl, uint64_t *bar, int t, const fx<K + 1> &dr, const fx<K + 1> &di,
-                      bool live) {
-    if (lane < MF_C && live) {
+  auto send_dot = [&](uint64_t *sl, uint64_t *bar, int t, const fx<K + 1> &dr, const fx<K + 1> &di) {
+    if (lane < MF_C) {
       const uint32_t ra = cl_mapa(smem_u32(sl + ((size_t)t * MF_C + rank) * SWD), lane);
       const uint32_t rb = cl_mapa(smem_u32(bar), lane);
 #pragma unroll
@@ -440,15 +477,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     const uint32_t bb = u & 1, par = (u >> 1) & 1;
     uint64_t *bar = bulk.bar + bb;
     uint64_t *sl = bulk.slot + (size_t)bb * a.maxown * MF_C * SWD;
-    const bool live = status_ok(a.status);
-    if (tid == 0 && live) mb_expect(bar, (uint32_t)(nb * MF_C * SWD * 8));
-    for (int cc = warp; cc < nb; cc += MF_WARPS) {
+    if (tid == 0) mb_expect(bar, (uint32_t)(nb * MF_C * SWD * 8));
+    for (int cc = warp; cc < nb; cc += MF_CW) {
       fx<K + 1> dr, di;
       warp_dot(q, colp(cf + cc), dr, di);
-      send_dot(sl, bar, cc, dr, di, live);
+      send_dot(sl, bar, cc, dr, di);
     }
     mb_wait(bar, par, a.status);
-    for (int cc = tid; cc < nb; cc += MF_THREADS) {
+    for (int cc = tid; cc < nb; cc += MF_CT) {
       fx<K + 1> tr, ti;
       fx_zero<K + 1>(tr);
       fx_zero<K + 1>(ti);
@@ -467,27 +503,41 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       sR[2 * cc + 1] = ix_narrow<K>(ti);
       if (rank == 0) out_r(k, cf + cc, tr, ti);
     }
-    __syncthreads();
-    for (int cc = warp; cc < nb; cc += MF_WARPS) warp_axpy(q, colp(cf + cc), sR[2 * cc], sR[2 * cc + 1]);
-    __syncthreads();  // sR, sQ and the slots are free for the next use
+    cw_sync();
+    for (int cc = warp; cc < nb; cc += MF_CW) warp_axpy(q, colp(cf + cc), sR[2 * cc], sR[2 * cc + 1]);
+    cw_sync();  // sR, sQ and the slots are free for the next use
   };
 
   // this CTA's rows of q_k from the publication slot into sQ (after its flag)
   auto load_q = [&](int k) {
     const fx<K> *qk = pubp(k);
-    for (int e = tid; e < 2 * nr; e += MF_THREADS) {
+    for (int e = tid; e < 2 * nr; e += MF_CT) {
       fx<K> v;
 #pragma unroll
       for (int w = 0; w < K; w++) v.w[w] = __ldcg(&qk[e].w[w]);
       sQ[e] = v;
     }
-    __syncthreads();
+    cw_sync();
   };
 
+  if (warp == MF_CW) {
+    // the publisher: releases the flags of this CTA's pivots in order
+    const int npub = no - ((no > 0 && owner(ncols - 1) == g) ? 1 : 0);
+    for (int pp = 0; pp < npub; pp++) {
+      const int ps = pp % MF_NPUB;
+      const bool got = mb_wait(pubFull + ps, (pp / MF_NPUB) & 1, a.status);
+      if (!__all_sync(0xffffffffu, got)) break;  // the warp leaves together
+      if (lane == 0) {
+        st_release(a.flags + (size_t)sPubJ[ps] * MF_C + rank, sPubAcc[ps] ? 1u : 2u);
+        mb_arrive(pubEmpty + ps);
+      }
+      __syncwarp();
+    }
+  } else {
   if (owner(0) == g && no > 0) {
     const uint32_t u = piv.use++;
     if (warp == 0) pivot(0, u);
-    __syncthreads();
+    cw_sync();
   }
 
   int kp = 0;  // first q not yet applied to the columns outside the current block
@@ -513,8 +563,6 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     const fx<K> *q;
     if (owner(k) == g) {
       q = colp(lcol(k));
-      // stop after a singular pivot of this cluster (decided by thread 0 for all)
-      if (__syncthreads_or(tid == 0 && !status_ok(a.status))) break;
     } else {
       int okv = 1;
       if (tid == 0) {
@@ -535,11 +583,11 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           }
           __nanosleep(32);
         }
-        okv = (v == 1) && status_ok(a.status);
+        okv = (v == 1);
       }
       // the one place a CTA leaves the loop early: uniform over the CTA; the
       // other CTAs of the cluster then find the status bad in their next wait
-      if (__syncthreads_or(tid == 0 && !okv)) break;
+      if (cw_sync_or(tid == 0 && !okv)) break;
       load_q(k);
       q = sQ;
     }
@@ -551,15 +599,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       const uint32_t bb = u & 1, par = (u >> 1) & 1;
       uint64_t *bar = la.bar + bb;
       uint64_t *sl = la.slot + (size_t)bb * B * MF_C * SWD;
-      const bool live = status_ok(a.status);
-      if (tid == 0 && live) mb_expect(bar, (uint32_t)(nla * MF_C * SWD * 8));
+      if (tid == 0) mb_expect(bar, (uint32_t)(nla * MF_C * SWD * 8));
       const int t = warp - (j1 % B);  // this warp's column j1 + t
       if (warp < B && t >= 0 && t < nla) {
         const int c = lcol(j1 + t);
         fx<K> *aj = colp(c);
         fx<K + 1> dr, di;
         warp_dot(q, aj, dr, di);
-        send_dot(sl, bar, t, dr, di, live);
+        send_dot(sl, bar, t, dr, di);
         mb_wait(bar, par, a.status);
         fx<K + 1> v[2];
 #pragma unroll
@@ -592,12 +639,14 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         }
       }
       piv.use++;
-      __syncthreads();  // q_{k+1} and the block's columns are visible to every warp
+      cw_sync();  // q_{k+1} and the block's columns are visible to every compute warp
     } else {
       bulk_apply(k, q, cf);
       kp = k + 1;
     }
   }
+  }  // compute warps
+  __syncthreads();
   if (!ok) atomicCAS(a.status, GN_OK, GN_ENONFINITE);
   // the residual column b - Q y back to global memory
   if (a.smem_cols && no > 0 && owner(ncols - 1) == g && status_ok(a.status)) {
