@@ -41,6 +41,17 @@ FX_HD ux<K> ix_abs(const fx<K> &a, uint64_t &neg) {
   return r;
 }
 
+// |a| as a signed N-limb value (a >= -2^(64N-1) + 1)
+template <int N>
+FX_HD fx<N> ix_abs_fx(const fx<N> &a) {
+  uint64_t n;
+  const ux<N> u = ix_abs<N>(a, n);
+  fx<N> r;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.w[i] = u.w[i];
+  return r;
+}
+
 // conditional two's-complement negation of an N-limb value
 template <int N>
 FX_HD void ix_cneg(fx<N> &a, uint64_t neg) {
@@ -101,6 +112,30 @@ FX_HD fx<K + 1> ix_mul_shift(const fx<K> &a, const fx<K> &b) {
   }
   ix_cneg<K + 1>(r, na ^ nb);
   return r;
+}
+
+// a * b exactly for signed KA- and KB-limb values, as KA+KB limbs (signed)
+template <int KA, int KB>
+FX_HD fx<KA + KB> ix_mul_full(const fx<KA> &a, const fx<KB> &b) {
+  uint64_t na, nb;
+  const ux<KA> ua = ix_abs<KA>(a, na);
+  const ux<KB> ub = ix_abs<KB>(b, nb);
+  fx<KA + KB> p;
+#pragma unroll
+  for (int i = 0; i < KA + KB; i++) p.w[i] = 0;
+#pragma unroll
+  for (int i = 0; i < KA; i++) {
+    u128_t carry = 0;
+#pragma unroll
+    for (int j = 0; j < KB; j++) {
+      u128_t t = (u128_t)ua.w[i] * ub.w[j] + p.w[i + j] + carry;
+      p.w[i + j] = (uint64_t)t;
+      carry = t >> 64;
+    }
+    p.w[i + KB] = (uint64_t)carry;
+  }
+  ix_cneg<KA + KB>(p, na ^ nb);
+  return p;
 }
 
 // |a|^2 exactly as 2K+1 limbs (unsigned, top limb zero)
@@ -170,6 +205,15 @@ FX_HD fx<K> ix_narrow(const fx<K + 1> &a) {
   fx<K> r;
 #pragma unroll
   for (int i = 0; i < K; i++) r.w[i] = a.w[i];
+  return r;
+}
+
+// the low N limbs of an M-limb value (caller guarantees it fits)
+template <int N, int M>
+FX_HD fx<N> ix_low(const fx<M> &a) {
+  fx<N> r;
+#pragma unroll
+  for (int i = 0; i < N; i++) r.w[i] = a.w[i];
   return r;
 }
 

@@ -35,6 +35,15 @@ static void run(const char *op) {
     for (int i = 0; i < K; i++) t.w[i] = a.w[i];
     gn::ux<K> y = gn::ix_rsqrt_frac<K>(t);
     for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)y.w[i]);
+  } else if (!strcmp(op, "mulf")) {
+    // a (K+1 limbs: a_0..a_{K-1} then one more) times b (K limbs)
+    gn::fx<K + 1> a1;
+    for (int i = 0; i < K; i++) a1.w[i] = a.w[i];
+    unsigned long long top;
+    scanf("%llx", &top);
+    a1.w[K] = top;
+    gn::fx<2 * K + 1> r = gn::ix_mul_full<K + 1, K>(a1, b);
+    for (int i = 0; i < 2 * K + 1; i++) printf("%llx ", (unsigned long long)r.w[i]);
   } else if (!strcmp(op, "bitlen")) {
     printf("%x ", gn::ix_bitlen<K>(a));
   }

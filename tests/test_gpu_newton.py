@@ -51,7 +51,7 @@ def gpu_lstsq(A, L, prec, arith="int"):
 
 @pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
-@pytest.mark.parametrize("m,n", [(1, 1), (7, 4), (40, 33), (300, 257), (513, 60)])
+@pytest.mark.parametrize("m,n", [(1, 1), (7, 4), (40, 33), (130, 127), (300, 257), (513, 60)])
 def test_lstsq_parity(prec, L, m, n, arith):
     rng = np.random.default_rng(m * 1000 + n)
     A = _rand_matrix(rng, m, n + 1, L)

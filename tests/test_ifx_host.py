@@ -97,6 +97,20 @@ def test_square_add_sub_sar_bitlen(harness, K):
             assert val(got) == want, kind
 
 
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_mul_full(harness, K):
+    """ix_mul_full: exact signed (K+1)-limb x K-limb products."""
+    rng = np.random.default_rng(70 + K)
+    cases = [(rand_signed(rng, K + 1, 64 * K + 40), rand_signed(rng, K)) for _ in range(200)]
+    cases += [(0, 5), (-1, -1), (-(1 << (64 * K + 40)), (1 << (64 * K - 2)) - 1)]
+    lines = []
+    for a, b in cases:
+        la = limbs(a, K + 1)
+        lines.append(f"mulf {K} " + " ".join("%x" % x for x in la[:K] + limbs(b, K) + la[K:]))
+    for (a, b), got in zip(cases, run(harness, lines)):
+        assert val(got) == a * b
+
+
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 9])
 def test_barrel_shifts(harness, N):
     """ix_sar (arithmetic) and ix_shl (bits above 64 N lost) for every shift
