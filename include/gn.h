@@ -178,6 +178,47 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
                     gn_report *report, void *cuda_stream);
 
 /*
+ * Batches: many independent square systems (N_s = n_s <= 128) advanced
+ * together (Section 4 steps on every system of the batch).  The systems are
+ * stored back to back in sparse distributed form (Section 1):
+ *   S          : number of systems.
+ *   h_sys_n    : [S], n_s in 1 .. 128; system s owns polynomials
+ *                [P_s, P_s + n_s) and variables [X_s, X_s + n_s) of the
+ *                concatenated vectors (P_s = X_s = n_0 + ... + n_{s-1}).
+ *   T          : total number of terms over all polynomials.
+ *   h_poly_ptr : [X+1] (X = sum of n_s) term ranges of the polynomials.
+ *   h_mono_ptr, h_exp, h_coef, coef_limbs : as for gn_system_create.
+ *   h_var      : variable indices LOCAL to each system, in [0, n_s).
+ * Returns GN_EINVAL for a malformed batch (as gn_system_create, per system).
+ * The paper treats one system at a time; batching is this library's.
+ */
+typedef struct gn_batch gn_batch;
+gn_status gn_batch_create(gn_batch **out, int32_t S, const int64_t *h_sys_n, int64_t T,
+                          const int64_t *h_poly_ptr, const int64_t *h_mono_ptr,
+                          const int32_t *h_var, const uint8_t *h_exp, const double *h_coef,
+                          int32_t coef_limbs);
+gn_status gn_batch_destroy(gn_batch *b);
+gn_status gn_batch_info(const gn_batch *b, int32_t *S, int64_t *X, int64_t *T, int64_t *nnz,
+                        int32_t *max_n);
+/*
+ * Take `steps` Gauss-Newton steps on every system of the batch, in place on
+ * d_x ([X] complex at precision prec, the systems' variables back to back).
+ * Each step is one CUDA graph: evaluation of all systems (integer mantissa
+ * arithmetic), then one persistent launch that solves every system's least
+ * squares problem by MGS and back substitution and adds dx.
+ *   d_status : [S] device int32, caller-owned, GN_OK on entry for the systems
+ *              to advance; a system whose least squares problem fails gets
+ *              GN_ESINGULAR or GN_ENONFINITE and is left alone afterwards.
+ *   d_norms  : [steps][S][2] device doubles (may be NULL): ||f(x_k)|| and
+ *              ||dx_k|| of each system at each step.
+ * Stream-ordered; does not synchronize.  The first call per precision times
+ * the candidate launch shapes of the solver on the batch (a few extra solves
+ * on a copy of x) and keeps the fastest.
+ */
+gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps, double *d_norms,
+                          int32_t *d_status, void *cuda_stream);
+
+/*
  * gn_eval_noalloc — the same evaluation as gn_eval, for callers that may not
  * allocate device memory when they evaluate (a host thread inside a CUDA
  * stream capture it does not own, a real-time loop that forbids allocator

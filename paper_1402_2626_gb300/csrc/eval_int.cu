@@ -154,11 +154,14 @@ __device__ __forceinline__ void cf_store_cascade(double *dst, const fx<L + 1> &r
   }
 }
 
+// J entry z goes to J[(col ldJ + row)], or to J[jz_out[z]] (complex entries)
+// when jz_out is given (the blocks of a batch)
 template <int L>
 __global__ void k_sum_jacobian_cf(int64_t nz, const int32_t *__restrict__ jz_row,
                                   const int32_t *__restrict__ jz_col,
                                   const int32_t *__restrict__ jz_ptr,
                                   const int32_t *__restrict__ jz_occ,
+                                  const int64_t *__restrict__ jz_out,
                                   const double *__restrict__ stage_d, double *__restrict__ J,
                                   int64_t ldJ, const int32_t *__restrict__ status) {
   constexpr int WS = CfStore<L>::WORDS;
@@ -175,12 +178,15 @@ __global__ void k_sum_jacobian_cf(int64_t nz, const int32_t *__restrict__ jz_row
   fx_zero<L + 1>(re);
   fx_zero<L + 1>(im);
   for (int p = p0; p < p1; p++) cf_accumulate<L>(re, im, cf_ld<L>(stage_d + (int64_t)__ldg(jz_occ + p) * WS), E);
-  cf_store_cascade<L>(J + ((int64_t)__ldg(jz_col + z) * ldJ + __ldg(jz_row + z)) * 2 * L, re, im, E, false);
+  const int64_t at = jz_out ? __ldg(jz_out + z) : (int64_t)__ldg(jz_col + z) * ldJ + __ldg(jz_row + z);
+  cf_store_cascade<L>(J + at * 2 * L, re, im, E, false);
 }
 
+// f_i goes to f[i], or to f[f_out[i]] (complex entries) when f_out is given
 template <int L>
 __global__ void k_sum_f_cf(int32_t N, const int32_t *__restrict__ poly_ptr,
-                           const double *__restrict__ stage_val, double *__restrict__ f, int neg,
+                           const double *__restrict__ stage_val, double *__restrict__ f,
+                           const int64_t *__restrict__ f_out, int neg,
                            const int32_t *__restrict__ status) {
   constexpr int WS = CfStore<L>::WORDS;
   const int i = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
@@ -208,30 +214,34 @@ __global__ void k_sum_f_cf(int32_t N, const int32_t *__restrict__ poly_ptr,
     re = ix_add<L + 1>(re, u);
     im = ix_add<L + 1>(im, v);
   }
-  if (lane == 0) cf_store_cascade<L>(f + (int64_t)i * 2 * L, re, im, E, neg != 0);
+  if (lane == 0) cf_store_cascade<L>(f + (f_out ? __ldg(f_out + i) : (int64_t)i) * 2 * L, re, im, E, neg != 0);
 }
 
 template <int L>
-static gn_status eval_int_impl(gn_system *s, Workspace *ws, const double *d_x, double *d_f, int neg_f,
-                               double *d_J, int64_t ldJ, cudaStream_t st) {
-  const int64_t W = 2 * L;
-  k_powers_cf<L><<<(s->n + 127) / 128, 128, 0, st>>>(d_x, s->n, s->pmax, ws->pow, ws->status);
-  if (s->T > 0)
-    k_monomials_cf<L><<<(unsigned)((s->T + 127) / 128), 128, 0, st>>>(
-        s->d_mono_off, s->d_occ, s->d_coef, s->T, ws->pow, s->n, ws->stage_val, ws->stage_d,
-        ws->status);
-  if (d_J) {
-    if (s->nz < (int64_t)s->N * s->n &&
-        cudaMemset2DAsync(d_J, sizeof(double) * W * ldJ, 0, sizeof(double) * W * s->N, s->n, st) !=
-            cudaSuccess)
-      return GN_ECUDA;
-    if (s->nz > 0)
-      k_sum_jacobian_cf<L><<<(unsigned)((s->nz + 127) / 128), 128, 0, st>>>(
-          s->nz, s->d_jz_row, s->d_jz_col, s->d_jz_ptr, s->d_jz_occ, ws->stage_d, d_J, ldJ,
-          ws->status);
-  }
-  if (d_f) k_sum_f_cf<L><<<(s->N + 3) / 4, 128, 0, st>>>(s->N, s->d_poly_ptr, ws->stage_val, d_f, neg_f, ws->status);
+static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
+  if (a.nvar > 0)
+    k_powers_cf<L><<<(unsigned)((a.nvar + 127) / 128), 128, 0, st>>>(a.x, (int32_t)a.nvar, a.pmax, a.pow,
+                                                                      a.status);
+  if (a.T > 0)
+    k_monomials_cf<L><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
+        a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+  if (a.J && a.nz > 0)
+    k_sum_jacobian_cf<L><<<(unsigned)((a.nz + 127) / 128), 128, 0, st>>>(
+        a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
+  if (a.f && a.npoly > 0)
+    k_sum_f_cf<L><<<(unsigned)((a.npoly + 3) / 4), 128, 0, st>>>((int32_t)a.npoly, a.poly_ptr, a.stage_val,
+                                                                 a.f, a.f_out, a.neg_f, a.status);
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
+gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st) {
+  if (a.kmax > KMAXI) return GN_EINVAL;
+  switch (L) {
+    case 1: return eval_int_raw<1>(a, st);
+    case 2: return eval_int_raw<2>(a, st);
+    case 4: return eval_int_raw<4>(a, st);
+  }
+  return GN_EINVAL;
 }
 
 gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
@@ -240,12 +250,36 @@ gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, i
   Workspace *ws;
   gn_status e = workspace_get(s, L, &ws);
   if (e) return e;
-  switch (L) {
-    case 1: return eval_int_impl<1>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
-    case 2: return eval_int_impl<2>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
-    case 4: return eval_int_impl<4>(s, ws, d_x, d_f, neg_f, d_J, ldJ, st);
-  }
-  return GN_EINVAL;
+  const int64_t W = 2 * L;
+  if (d_J && s->nz < (int64_t)s->N * s->n &&
+      cudaMemset2DAsync(d_J, sizeof(double) * W * ldJ, 0, sizeof(double) * W * s->N, s->n, st) !=
+          cudaSuccess)
+    return GN_ECUDA;
+  EvalArgs a;
+  a.x = d_x;
+  a.nvar = s->n;
+  a.pmax = s->pmax;
+  a.kmax = s->kmax;
+  a.pow = ws->pow;
+  a.T = s->T;
+  a.mono_off = s->d_mono_off;
+  a.occ = s->d_occ;
+  a.coef = s->d_coef;
+  a.stage_val = ws->stage_val;
+  a.stage_d = ws->stage_d;
+  a.nz = s->nz;
+  a.jz_row = s->d_jz_row;
+  a.jz_col = s->d_jz_col;
+  a.jz_ptr = s->d_jz_ptr;
+  a.jz_occ = s->d_jz_occ;
+  a.J = d_J;
+  a.ldJ = ldJ;
+  a.npoly = s->N;
+  a.poly_ptr = s->d_poly_ptr;
+  a.f = d_f;
+  a.neg_f = neg_f;
+  a.status = ws->status;
+  return launch_eval_int_raw(L, a, st);
 }
 
 }  // namespace gn

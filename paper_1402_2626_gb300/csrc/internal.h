@@ -61,6 +61,29 @@ gn_status launch_eval(gn_system *s, int L, const double *d_x, double *d_f, int n
 // eval_int.cu: integer mantissas with one exponent per complex value
 gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
                           double *d_J, int64_t ldJ, cudaStream_t st);
+// every array of one evaluation, for callers with their own layout (batches)
+struct EvalArgs {
+  const double *x = nullptr;  // [nvar] complex
+  int64_t nvar = 0;
+  int32_t pmax = 1, kmax = 0;
+  double *pow = nullptr, *stage_val = nullptr, *stage_d = nullptr;
+  int64_t T = 0;
+  const int32_t *mono_off = nullptr;
+  const uint32_t *occ = nullptr;  // (variable << 8) | exponent, variables in [0, nvar)
+  const double *coef = nullptr;   // [4][2][T]
+  int64_t nz = 0;
+  const int32_t *jz_row = nullptr, *jz_col = nullptr, *jz_ptr = nullptr, *jz_occ = nullptr;
+  const int64_t *jz_out = nullptr;  // complex-entry offsets of the J entries (or null: col ldJ + row)
+  double *J = nullptr;
+  int64_t ldJ = 0;
+  int64_t npoly = 0;
+  const int32_t *poly_ptr = nullptr;
+  double *f = nullptr;
+  const int64_t *f_out = nullptr;  // complex-entry offsets of f (or null: i)
+  int neg_f = 0;
+  const int32_t *status = nullptr;
+};
+gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st);
 // whether the system's arithmetic evaluates (eval_int) or solves (lstsq) on
 // integer mantissas at precision L
 inline bool eval_int(const gn_system *s, int L) {

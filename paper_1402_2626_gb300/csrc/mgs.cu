@@ -30,6 +30,7 @@
 
 #include <mutex>
 
+#include "bs.cuh"
 #include "ifx.cuh"
 #include "internal.h"
 #include "mw.cuh"

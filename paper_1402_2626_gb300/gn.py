@@ -33,8 +33,8 @@ REPORT_MAX = 64
 
 # exported symbols declared in include/gn.h
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
-           "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_status_str", "gn_version",
-           "gn_eval_noalloc")
+           "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_batch_create", "gn_batch_destroy",
+           "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc")
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
@@ -87,6 +87,16 @@ def load_library(path: str = LIB_PATH):
         L.gn_mgs.restype = C.c_int
         L.gn_newton.argtypes = [vp, C.c_int, vp, C.c_int32, dp, C.POINTER(Report), vp]
         L.gn_newton.restype = C.c_int
+        L.gn_batch_create.argtypes = [C.POINTER(vp), C.c_int32, i64p, C.c_int64, i64p, i64p,
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
+                                      C.POINTER(C.c_double), C.c_int32]
+        L.gn_batch_create.restype = C.c_int
+        L.gn_batch_destroy.argtypes = [vp]
+        L.gn_batch_destroy.restype = C.c_int
+        L.gn_batch_info.argtypes = [vp, C.POINTER(C.c_int32), i64p, i64p, i64p, C.POINTER(C.c_int32)]
+        L.gn_batch_info.restype = C.c_int
+        L.gn_batch_newton.argtypes = [vp, C.c_int, vp, C.c_int32, vp, vp, vp]
+        L.gn_batch_newton.restype = C.c_int
         L.gn_status_str.argtypes = [C.c_int]
         L.gn_status_str.restype = C.c_char_p
         L.gn_version.restype = C.c_int32
@@ -200,3 +210,57 @@ class System:
         if raise_on_error and st != 0:
             raise GnError(st, "gn_newton")
         return out
+
+
+class Batch:
+    """Independent square systems advanced together (owns a gn_batch)."""
+
+    def __init__(self, batch: inputs.Batch, coef_limbs: int = 4):
+        L = load_library()
+        self.S, self.X = batch.S, int(batch.sys_var[-1])
+        self._keep = [np.ascontiguousarray(np.diff(batch.sys_var), np.int64),
+                      np.ascontiguousarray(batch.poly_ptr, np.int64),
+                      np.ascontiguousarray(batch.mono_ptr, np.int64),
+                      np.ascontiguousarray(batch.var, np.int32),
+                      np.ascontiguousarray(batch.exp, np.uint8),
+                      np.ascontiguousarray(batch.coef[:, :, :coef_limbs], np.float64)]
+        ns, pp, mp, var, ex, cf = self._keep
+        h = C.c_void_p()
+        st = L.gn_batch_create(C.byref(h), batch.S, ns.ctypes.data_as(C.POINTER(C.c_int64)), batch.T,
+                               pp.ctypes.data_as(C.POINTER(C.c_int64)),
+                               mp.ctypes.data_as(C.POINTER(C.c_int64)),
+                               var.ctypes.data_as(C.POINTER(C.c_int32)),
+                               ex.ctypes.data_as(C.POINTER(C.c_uint8)),
+                               cf.ctypes.data_as(C.POINTER(C.c_double)), coef_limbs)
+        _check(st, "gn_batch_create")
+        self._keep = None  # the library copied what it needs
+        self._h = h
+        self._lib = L
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gn_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        S, mx = C.c_int32(), C.c_int32()
+        X, T, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(self._lib.gn_batch_info(self._h, C.byref(S), C.byref(X), C.byref(T), C.byref(nnz),
+                                       C.byref(mx)), "gn_batch_info")
+        return dict(S=S.value, X=X.value, T=T.value, nnz=nnz.value, max_n=mx.value)
+
+    def newton(self, prec, x, steps, status, norms=None, stream=None):
+        """``steps`` Gauss-Newton steps on every system, in place on x [X,2,L];
+        status [S] int32 (GN_OK on entry) and norms [steps,S,2] float64 are
+        CUDA tensors the call writes; stream-ordered, no synchronisation."""
+        if not status.is_cuda or str(status.dtype) != "torch.int32":
+            raise ValueError("status must be an int32 CUDA tensor")
+        _check(self._lib.gn_batch_newton(self._h, PREC[prec], _ptr(x), steps, _ptr(norms),
+                                         C.c_void_p(status.data_ptr()), _stream(stream)),
+               "gn_batch_newton")

@@ -50,6 +50,9 @@ import numpy as np
 BASE_SEED = 0x14022626
 
 __all__ = [
+    "Batch",
+    "random_batch",
+    "batch_workload",
     "System",
     "random_system",
     "workload",
@@ -263,6 +266,234 @@ def _set_constants(s: System) -> None:
             s.coef[t, 1, :] = cascade_from_fraction(im, 4)
 
 
+# -- batches of independent systems --------------------------------------------
+
+
+@dataclass
+class Batch:
+    """Independent square systems stored back to back in sparse distributed form.
+
+    System ``s`` owns polynomials ``[sys_poly[s], sys_poly[s+1])`` and
+    variables ``[sys_var[s], sys_var[s+1])`` of the concatenated vectors;
+    ``var`` holds variable indices local to each system.  The other arrays
+    follow :class:`System`.
+    """
+
+    S: int
+    sys_poly: np.ndarray  # int64 [S+1]
+    sys_var: np.ndarray  # int64 [S+1]
+    poly_ptr: np.ndarray  # int64 [P+1]
+    mono_ptr: np.ndarray  # int64 [T+1]
+    var: np.ndarray  # int32 [nnz], local
+    exp: np.ndarray  # uint8 [nnz]
+    coef: np.ndarray  # float64 [T, 2, 4]
+    xstar: np.ndarray  # float64 [X, 2]
+    x0: np.ndarray  # float64 [X, 2]
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> np.ndarray:
+        return np.diff(self.sys_var)
+
+    @property
+    def T(self) -> int:
+        return int(self.mono_ptr.shape[0] - 1)
+
+    def point(self, which: str, L: int) -> np.ndarray:
+        src = self.xstar if which == "xstar" else self.x0
+        out = np.zeros((src.shape[0], 2, L), dtype=np.float64)
+        out[:, :, 0] = src
+        return out
+
+    def system(self, s: int) -> System:
+        """System ``s`` on its own (arrays rebased to start at 0)."""
+        p0, p1 = int(self.sys_poly[s]), int(self.sys_poly[s + 1])
+        t0, t1 = int(self.poly_ptr[p0]), int(self.poly_ptr[p1])
+        o0, o1 = int(self.mono_ptr[t0]), int(self.mono_ptr[t1])
+        v0, v1 = int(self.sys_var[s]), int(self.sys_var[s + 1])
+        return System(N=p1 - p0, n=v1 - v0, poly_ptr=self.poly_ptr[p0:p1 + 1] - t0,
+                      mono_ptr=self.mono_ptr[t0:t1 + 1] - o0, var=self.var[o0:o1].copy(),
+                      exp=self.exp[o0:o1].copy(), coef=self.coef[t0:t1].copy(),
+                      xstar=self.xstar[v0:v1].copy(), x0=self.x0[v0:v1].copy(),
+                      name=f"batch[{s}]")
+
+
+def _supports(rng, k, n):
+    """Uniform k-subsets of range(n) (n <= 128) as 128-bit masks (lo, hi), one
+    per entry of ``k``: Floyd's sampling, vectorised over the subsets."""
+    T = k.shape[0]
+    lo = np.zeros(T, dtype=np.uint64)
+    hi = np.zeros(T, dtype=np.uint64)
+    for i in range(int(k.max()) if T else 0):
+        act = i < k
+        j = n - k + i  # candidates [0, j]
+        t = np.minimum((rng.random(T) * (j + 1)).astype(np.int64), j)
+        sh = (t & 63).astype(np.uint64)
+        up = t >= 64
+        taken = np.where(up, hi >> sh, lo >> sh) & np.uint64(1)
+        pick = np.where(taken.astype(bool), j, t)
+        bit = np.left_shift(np.uint64(1), (pick & 63).astype(np.uint64)) * act.astype(np.uint64)
+        up = pick >= 64
+        hi |= np.where(up, bit, np.uint64(0))
+        lo |= np.where(up, np.uint64(0), bit)
+    return lo, hi
+
+
+def _mask_bits(lo, hi, n):
+    """(subset index, variable) pairs of the masks, variables ascending within a subset."""
+    b = np.stack([lo, hi], axis=1).view(np.uint8).reshape(-1, 16)
+    bits = np.unpackbits(b, axis=1, bitorder="little")[:, :n]
+    t, v = np.nonzero(bits)
+    return t, v.astype(np.int32)
+
+
+def _mix(x):
+    """64-bit mixing (splitmix64 finaliser) of uint64 arrays."""
+    x = x.copy()
+    x ^= x >> np.uint64(30)
+    x *= np.uint64(0xBF58476D1CE4E5B9)
+    x ^= x >> np.uint64(27)
+    x *= np.uint64(0x94D049BB133111EB)
+    x ^= x >> np.uint64(31)
+    return x
+
+
+def _exact_sums(values, starts):
+    """Exact sums of the doubles ``values`` over the consecutive segments that
+    begin at ``starts``, each rounded to a 4-limb nearest cascade.  Every
+    double is split into four integer chunks on grids of 2^-40 .. 2^-160
+    (exact for values of magnitude >= 2^-107, checked); chunk sums are exact
+    in int64 (|chunk| < 2^41, fewer than 2^22 terms per segment) and are
+    combined in Python integers."""
+    rest = values.astype(np.float64)
+    sums = []
+    for c in range(4):
+        q = np.trunc(np.ldexp(rest, 40 * (c + 1)))
+        sums.append(np.add.reduceat(q.astype(np.int64), starts))
+        rest = rest - np.ldexp(q, -40 * (c + 1))
+    if np.any(rest != 0.0):
+        raise ValueError("a term is not exact on the 2^-160 grid")
+    out = np.zeros((starts.size, 4), dtype=np.float64)
+    for i in range(starts.size):
+        tot = (int(sums[0][i]) << 120) + (int(sums[1][i]) << 80) + (int(sums[2][i]) << 40) + int(sums[3][i])
+        for l in range(4):  # nearest double of what is left (int -> float rounds to
+            f = float(tot)  # nearest), then the exact remainder
+            out[i, l] = math.ldexp(f, -160)
+            tot -= int(f)
+    return out
+
+
+def _batch_system(n, seq, M_frac, k_max, dmax):
+    """One system of a batch from its own seed sequence (see random_batch)."""
+    r_sup, r_exp, r_coef, r_root, r_pert = [np.random.default_rng(q) for q in seq.spawn(5)]
+    quarter = r_root.integers(0, 4, size=n)  # x*_j = i^quarter
+    xstar = np.stack([np.array([1.0, 0.0, -1.0, 0.0])[quarter],
+                      np.array([0.0, 1.0, 0.0, -1.0])[quarter]], axis=1)
+    phi = 2.0 * math.pi * r_pert.random(n)
+    x0 = xstar + 1e-6 * np.stack([np.cos(phi), np.sin(phi)], axis=-1)
+    M = r_sup.integers(int(math.ceil(M_frac[0] * n)), int(math.floor(M_frac[1] * n)) + 1, size=n)
+    Tm = int(M.sum())
+    poly_of = np.repeat(np.arange(n), M)
+    kk = r_sup.integers(2, min(k_max, n) + 1, size=Tm)
+    lo, hi = _supports(r_sup, kk, n)
+    emask = (np.left_shift(1, 2 * kk) - 1).astype(np.int64)
+    ek = r_exp.integers(0, 1 << 32, size=Tm, dtype=np.int64) & emask
+    for _ in range(100):  # distinct monomials within a polynomial: redraw duplicates
+        h = _mix(_mix(_mix(lo ^ _mix(poly_of.astype(np.uint64))) ^ hi) ^ ek.astype(np.uint64))
+        _, first = np.unique(h, return_index=True)
+        dup = np.ones(Tm, dtype=bool)
+        dup[first] = False
+        if not dup.any():
+            break
+        idx = np.nonzero(dup)[0]
+        lo[idx], hi[idx] = _supports(r_sup, kk[idx], n)
+        ek[idx] = r_exp.integers(0, 1 << 32, size=idx.size, dtype=np.int64) & emask[idx]
+    else:
+        raise RuntimeError("could not draw distinct monomials")
+    t_of, v = _mask_bits(lo, hi, n)
+    slot = np.arange(t_of.size) - np.repeat(np.concatenate([[0], np.cumsum(kk)[:-1]]), kk)
+    e = (((ek[t_of] >> (2 * slot)) & 3) % dmax + 1).astype(np.uint8)
+    cth = 2.0 * math.pi * r_coef.random(Tm)
+    c = np.stack([np.cos(cth), np.sin(cth)], axis=1)
+    ph = np.zeros(Tm, dtype=np.int64)  # x*^a = i^ph
+    np.add.at(ph, t_of, quarter[v] * e)
+    ph %= 4
+    re = np.choose(ph, [c[:, 0], -c[:, 1], -c[:, 0], c[:, 1]])
+    im = np.choose(ph, [c[:, 1], c[:, 0], -c[:, 1], -c[:, 0]])
+    starts = np.concatenate([[0], np.cumsum(M)[:-1]])
+    const = np.stack([-_exact_sums(re, starts), -_exact_sums(im, starts)], axis=1)  # [n, 2, 4]
+    return M, kk, v, e, c, const, xstar, x0
+
+
+def _batch_chunk(args):
+    ns, seqs, M_frac, k_max, dmax = args
+    return [_batch_system(int(n), q, M_frac, k_max, dmax) for n, q in zip(ns, seqs)]
+
+
+def random_batch(S: int, seed: int, n_range=(16, 128), M_frac=(0.5, 2.0), k_max: int = 16,
+                 dmax: int = 4, workers: int = 0) -> Batch:
+    """``S`` independent square systems (N = n).  n is uniform in ``n_range``;
+    each polynomial has M uniform in [ceil(M_frac[0] n), floor(M_frac[1] n)]
+    non-constant monomials plus a constant term; a monomial has k uniform in
+    [2, min(k_max, n)] distinct variables (a uniform k-subset) with exponents
+    uniform in 1..dmax (dmax <= 4); monomials within a polynomial are
+    distinct; coefficients are unit-modulus.  The root x* has components in
+    {1, i, -1, -i}, so each term c_t x*^a is the double c_t turned by a
+    multiple of 90 degrees and the constant term -sum_t c_t x*^a is an exact
+    sum of doubles, stored as a 4-limb cascade; x0 = x* + 1e-6 exp(i phi).
+    System s draws from its own seed sequence (SeedSequence(seed).spawn(S)[s]),
+    so it is the same whatever S' >= s+1 and however many worker processes
+    (``workers``, spawned) build the batch."""
+    if not 1 <= dmax <= 4:
+        raise ValueError("dmax must be in 1..4")
+    root = np.random.SeedSequence(seed)
+    r_n = np.random.default_rng(root.spawn(1)[0])
+    n_s = r_n.integers(n_range[0], n_range[1] + 1, size=S).astype(np.int64)
+    seqs = np.random.SeedSequence(seed + (1 << 40)).spawn(S)
+    if workers > 1 and S >= 64:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        chunks = np.array_split(np.arange(S), workers * 4)
+        jobs = [(n_s[c], [seqs[i] for i in c], M_frac, k_max, dmax) for c in chunks if c.size]
+        with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = [r for chunk in ex.map(_batch_chunk, jobs) for r in chunk]
+    else:
+        parts = _batch_chunk((n_s, seqs, M_frac, k_max, dmax))
+    poly_ptr_l, mono_ptr_l, var_l, exp_l, coef_l = [np.zeros(1, np.int64)], [np.zeros(1, np.int64)], [], [], []
+    xs_l, x0_l = [], []
+    tcount = occ = 0
+    for (M, kk, v, e, c, const, xstar, x0), n in zip(parts, n_s):
+        n = int(n)
+        Tm = int(M.sum())
+        poly_of = np.repeat(np.arange(n), M)
+        starts = np.concatenate([[0], np.cumsum(M)[:-1]])
+        # per polynomial: its M monomials, then its constant term
+        pos = np.arange(Tm) + poly_of
+        cpos = starts + M + np.arange(n)
+        klen = np.zeros(Tm + n, dtype=np.int64)
+        klen[pos] = kk
+        mono_ptr_l.append(occ + np.cumsum(klen))
+        occ += int(kk.sum())
+        poly_ptr_l.append(tcount + cpos + 1)
+        cf_ = np.zeros((Tm + n, 2, 4), dtype=np.float64)
+        cf_[pos, 0, 0] = c[:, 0]
+        cf_[pos, 1, 0] = c[:, 1]
+        cf_[cpos] = const
+        coef_l.append(cf_)
+        var_l.append(v)
+        exp_l.append(e)
+        xs_l.append(xstar)
+        x0_l.append(x0)
+        tcount += Tm + n
+    sys_var = np.concatenate([[0], np.cumsum(n_s)]).astype(np.int64)
+    return Batch(S=S, sys_poly=sys_var.copy(), sys_var=sys_var,
+                 poly_ptr=np.concatenate(poly_ptr_l), mono_ptr=np.concatenate(mono_ptr_l),
+                 var=np.concatenate(var_l).astype(np.int32), exp=np.concatenate(exp_l),
+                 coef=np.concatenate(coef_l), xstar=np.concatenate(xs_l), x0=np.concatenate(x0_l),
+                 meta=dict(S=S, seed=seed, n_range=n_range, M_frac=M_frac, k_max=k_max, dmax=dmax))
+
+
 # -- named workloads ----------------------------------------------------------
 
 WORKLOADS = {
@@ -271,6 +502,23 @@ WORKLOADS = {
     # plain Gauss-Newton at scale (D, DD, QD)
     "gn256": dict(N=256, n=256, M=256, k=16, dmax=5, steps=4, config=2),
 }
+
+BATCH_WORKLOADS = {
+    # batched Gauss-Newton, complex DD: 4096 systems, n in [16, 128]
+    "batch4096": dict(S=4096, n_range=(16, 128), config=3),
+}
+
+
+@functools.lru_cache(maxsize=4)
+def batch_workload(name: str, S: int | None = None, index: int = 0) -> Batch:
+    """Named batch (cached); ``S`` overrides the number of systems (a prefix
+    of the same stream of sizes is not kept: a different S draws afresh)."""
+    import os
+
+    w = BATCH_WORKLOADS[name]
+    seed = BASE_SEED + 1000 * w["config"] + index
+    S = w["S"] if S is None else S
+    return random_batch(S, seed, n_range=w["n_range"], workers=min(16, os.cpu_count() or 1) if S >= 512 else 0)
 
 
 @functools.lru_cache(maxsize=8)

@@ -80,3 +80,6 @@ def test_calls_reject_null_handles(lib):
     assert lib.gn_system_destroy(None) == 1
     assert lib.gn_system_set_arith(None, 0) == 1
     assert lib.gn_mgs(None, 2, 4, 3, None, 4, None, None, None) == 1
+    assert lib.gn_batch_newton(None, 2, None, 1, None, None, None) == 1
+    assert lib.gn_batch_destroy(None) == 1
+    assert lib.gn_batch_create(None, 1, None, 0, None, None, None, None, None, 1) == 1
