@@ -242,6 +242,7 @@ def main():
     ap.add_argument("--prec", default="dd", choices=list(PRECS))
     ap.add_argument("--no-extras", action="store_true", help="skip per-precision breakdowns")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -327,6 +328,8 @@ def main():
     roofline = None
     if rank == 0 and not args.no_extras:
         extras, roofline = breakdown(S, system, dev, flush, args)
+        if not args.no_batch:
+            extras["batched"] = batched(dev, args)
 
     if rank == 0:
         line = {
@@ -348,6 +351,76 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batched(dev, args, loop_sample=64):
+    """The batched configuration: 4096 independent systems (n in [16, 128],
+    M in [n/2, 2n] per polynomial, k in [2, 16], exponents 1..4), complex DD,
+    one graph per Newton step; against the same systems stepped one at a time
+    through the single-system path (measured on ``loop_sample`` systems spread
+    over the sizes, scaled to the batch)."""
+    import numpy as np
+    import torch
+
+    from paper_1402_2626_gb300 import gn, inputs
+
+    t0 = time.perf_counter()
+    b = inputs.batch_workload("batch4096")
+    gen_s = time.perf_counter() - t0
+    g = gn.Batch(b)
+    L = 2
+    x0 = torch.tensor(b.point("x0", L), device=dev)
+    x = x0.clone()
+    status = torch.zeros((b.S,), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    g.newton("dd", x, 1, status)  # tunes the solver's launch, captures the step
+    torch.cuda.synchronize()
+    reps = max(3, min(args.steps, 10))
+    ms = []
+    for _ in range(reps):
+        x.copy_(x0)
+        status.zero_()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        g.newton("dd", x, 1, status)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(e))
+    step_ms = statistics.median(ms)
+    ok = not bool(status.any().item())
+    g.close()
+    # the plain path, one system at a time, on systems spread over the sizes
+    order = np.argsort(b.n, kind="stable")
+    pick = order[np.linspace(0, b.S - 1, loop_sample).astype(int)]
+    loop_ms = []
+    for s in pick:
+        sy = b.system(int(s))
+        S1 = gn.System(sy)
+        xs0 = torch.tensor(sy.point("x0", L), device=dev)
+        xs = xs0.clone()
+        S1.newton("dd", xs, 1)  # captures its step
+        xs.copy_(xs0)
+        torch.cuda.synchronize()
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S1.newton("dd", xs, 1)
+        e.record(stream)
+        torch.cuda.synchronize()
+        loop_ms.append(a.elapsed_time(e))
+        S1.close()
+    loop_total_ms = float(np.mean(loop_ms)) * b.S
+    imad = sum(algorithmic_imad_mgs(int(n), int(n) + 1, L) for n in b.n)
+    return {"workload": "batch4096", "systems": b.S, "terms": b.T, "precision": "dd",
+            "ms_per_step": step_ms, "system_steps_per_s": b.S / (step_ms / 1e3), "all_ok": ok,
+            "loop_plain_ms_per_step_est": loop_total_ms,
+            "loop_plain_sample": f"{loop_sample} systems spread over the sizes, mean x {b.S}",
+            "speedup_vs_loop": loop_total_ms / step_ms,
+            "mgs_imad_per_step": imad,
+            "mgs_imad_rate_lower_bound": {"achieved": imad / (step_ms / 1e3) / 1e9, "unit": "G IMAD/s",
+                                          "peak": IMAD_PEAK_GINSTR,
+                                          "frac": imad / (step_ms / 1e3) / 1e9 / IMAD_PEAK_GINSTR,
+                                          "note": "MGS work only over the whole step time (evaluation not counted)"},
+            "generate_s": gen_s}
 
 
 def breakdown(S, system, dev, flush, args):
