@@ -64,7 +64,9 @@ __global__ void k_powers_cf(const double *__restrict__ x, int32_t n, int32_t pma
   }
 }
 
-template <int L>
+// KM: the longest support the launch handles (the forward products of one
+// monomial live in a KM-entry per-thread array)
+template <int L, int KM>
 __global__ void __launch_bounds__(128) k_monomials_cf(
     const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
     const double *__restrict__ coef, int64_t T, const double *__restrict__ pow, int32_t n,
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(128) k_monomials_cf(
     cf_st<L>(stage_val + t * WS, a);
     return;
   }
-  cf<L> F[KMAXI];
+  cf<L> F[KM];
   F[0] = a;
   for (int s = 1; s < k; s++) {
     int v = (int)(__ldg(occ + o0 + s - 1) >> 8);
@@ -222,9 +224,14 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
   if (a.nvar > 0)
     k_powers_cf<L><<<(unsigned)((a.nvar + 127) / 128), 128, 0, st>>>(a.x, (int32_t)a.nvar, a.pmax, a.pow,
                                                                       a.status);
-  if (a.T > 0)
-    k_monomials_cf<L><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
-        a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+  if (a.T > 0) {
+    if (a.kmax <= 16)
+      k_monomials_cf<L, 16><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
+          a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+    else
+      k_monomials_cf<L, KMAXI><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
+          a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+  }
   if (a.J && a.nz > 0)
     k_sum_jacobian_cf<L><<<(unsigned)((a.nz + 127) / 128), 128, 0, st>>>(
         a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
