@@ -66,6 +66,11 @@ def lib():
             L.o_mgs.argtypes = [C.c_int, C.c_int32, C.c_int32, dp, C.c_int64, dp, C.c_int32, C.c_int]
             L.o_backsub.argtypes = [C.c_int, C.c_int32, dp, C.c_int32, dp]
             L.o_axpy_update.argtypes = [C.c_int, C.c_int32, dp, dp]
+            L.o_adjoint.argtypes = [C.c_int, C.c_int32, C.c_int32, dp, C.c_int64, dp, C.c_int32,
+                                    dp, dp, dp]
+            L.o_monomials.argtypes = [C.c_int, C.c_int64, i64p, C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_uint8), dp, dp]
+            L.o_coef_grad.argtypes = [C.c_int, C.c_int32, i64p, dp, dp, dp]
             _lib = L
     return _lib
 
@@ -216,6 +221,49 @@ def newton(system, x0, L: int, steps: int, nthreads: int = 1):
         hist.append((float(np.sqrt((f[:, :, 0] ** 2).sum())),
                      float(np.sqrt((dx[:, :, 0] ** 2).sum()))))
     return x, hist
+
+
+# -- adjoint (gradient with respect to the coefficients) ------------------------
+
+
+def monomials(system, x, L: int) -> np.ndarray:
+    """m_t = x^{a_t} for every term ([T, 2, L]; 1 for a constant term)."""
+    x = _f64(np.asarray(x)[..., :L]).reshape(system.n, 2, L)
+    out = np.zeros((system.T, 2, L))
+    st = lib().o_monomials(L, system.T, _p(system.mono_ptr, C.c_int64), _p(system.var, C.c_int32),
+                           _p(system.exp, C.c_uint8), _p(x), _p(out))
+    if st:
+        raise OracleError(st, "monomials")
+    return out
+
+
+def adjoint(system, x, g, L: int, nthreads: int = 1):
+    """Gradient of a real loss with respect to every coefficient at a root x.
+
+    ``g`` ([n, 2, L]) is the loss gradient dL/dRe x + i dL/dIm x at x.  The
+    root moves by dx = -J^+ (df/dc) dc (implicit function theorem at the
+    Gauss-Newton fixed point of Section 4, J = QR as in Section 3), so the
+    coefficient gradient is grad_t = -lambda_{i(t)} conj(x^{a_t}) with
+    lambda = Q R^{-H} g.  Every coefficient, the constant terms included,
+    counts as an independent input.  Returns (grad [T, 2, L], lambda [N, 2, L]).
+    """
+    n, N = system.n, system.N
+    x = _f64(np.asarray(x)[..., :L]).reshape(n, 2, L)
+    g = _f64(np.asarray(g)[..., :L]).reshape(n, 2, L)
+    f, J, _ = evaluate(system, x, L, "reverse", nthreads=nthreads)
+    Q, R = mgs(augmented(f, J), L, nthreads=nthreads)  # leading n columns: J = QR
+    Qcm = np.ascontiguousarray(Q[:, :n].transpose(1, 0, 2, 3))
+    Rcm = np.ascontiguousarray(R[:n, :n].transpose(1, 0, 2, 3))
+    w = np.zeros((max(n, 1), 2, L))
+    lam = np.zeros((max(N, 1), 2, L))
+    st = lib().o_adjoint(L, N, n, _p(Qcm), N, _p(Rcm), n, _p(g), _p(w), _p(lam))
+    if st:
+        raise OracleError(st, "adjoint")
+    lam = lam[:N]
+    mono = monomials(system, x, L)
+    grad = np.zeros((system.T, 2, L))
+    lib().o_coef_grad(L, N, _p(system.poly_ptr, C.c_int64), _p(lam), _p(mono), _p(grad))
+    return grad, lam
 
 
 def to_complex(a) -> np.ndarray:

@@ -35,6 +35,11 @@
  *   conjugated inner products, eq. 2 for y and z, and back substitution
  *   r_ll x_l = y_l - sum_{j>l} r_lj x_j (the reading of eq. 5).
  *
+ *   Coefficient gradient at a root (an extension past the paper: the
+ *   implicit function theorem at the Newton fixed point of Section 4):
+ *   forward substitution with R^H, lambda = Q w, monomial values by the
+ *   definition, grad_t = -lambda_i conj(x^{a_t}).
+ *
  * Layout of a complex number at precision L: 2L doubles, the L limbs of the
  * real part then the L limbs of the imaginary part.
  *
@@ -700,6 +705,79 @@ int o_backsub(int L, int32_t n, const double *R, int32_t ldr, double *x) {
 int o_axpy_update(int L, int32_t n, double *x, const double *dx) {
   const int64_t W = 2 * L;
   for (int i = 0; i < n; i++) c_add(L, x + i * W, dx + i * W, x + i * W);
+  return O_OK;
+}
+
+/*
+ * Adjoint of a converged Gauss-Newton solve (the gradient of a real loss
+ * with respect to the coefficients, by the implicit function theorem applied
+ * to the Newton fixed point of Section 4; the paper stops at the forward
+ * solve, so this is an extension).
+ *
+ * At a root x of f(x; c) = 0 with J of full column rank, a change dc of the
+ * coefficients moves the root by dx = -J^+ (df/dc) dc, J^+ = R^-1 Q^H for
+ * the factors J = QR of Section 3.  For a real loss with gradient
+ * g = dL/dRe x + i dL/dIm x, the gradient with respect to c is
+ * sum_j g_j conj(dx_j/dc) = -((J^+)^H g)_i conj(df_i/dc) for a coefficient c
+ * of polynomial i, and df_i/dc_t = x^{a_t}.  Hence three steps:
+ *   o_adjoint:    R^H w = g by forward substitution,
+ *                 w_l = (g_l - sum_{j<l} conj(r_jl) w_j) / r_ll (r_ll real),
+ *                 then lambda = Q w, lambda_i = sum_l q_il w_l (l ascending);
+ *   o_monomials:  m_t = x^{a_t}, each power by repeated multiplication in
+ *                 support order (the definition of eq. 1);
+ *   o_coef_grad:  grad_t = -lambda_{i(t)} conj(m_t).
+ * Q (m x n) and R (n x n, upper part read) are column-major as o_mgs leaves
+ * them: the first n columns of the overwritten [J b] and of its R.
+ */
+int o_adjoint(int L, int32_t m, int32_t n, const double *Q, int64_t ldq, const double *R,
+              int32_t ldr, const double *g, double *w, double *lam) {
+  if (L != 1 && L != 2 && L != 4) return O_EINVAL;
+  const int64_t W = 2 * L;
+  for (int l = 0; l < n; l++) {
+    double acc[8], p[8];
+    memcpy(acc, g + (int64_t)l * W, sizeof(double) * W);
+    for (int j = 0; j < l; j++) {
+      c_conj_mul(L, R + ((int64_t)l * ldr + j) * W, w + (int64_t)j * W, p);
+      c_sub(L, acc, p, acc);
+    }
+    int st = c_div_real(L, acc, R + ((int64_t)l * ldr + l) * W, w + (int64_t)l * W);
+    if (st) return st;
+  }
+  for (int i = 0; i < m; i++) {
+    double acc[8], p[8];
+    c_zero(L, acc);
+    for (int l = 0; l < n; l++) {
+      c_mul(L, Q + ((int64_t)l * ldq + i) * W, w + (int64_t)l * W, p);
+      c_add(L, acc, p, acc);
+    }
+    memcpy(lam + (int64_t)i * W, acc, sizeof(double) * W);
+  }
+  return O_OK;
+}
+
+int o_monomials(int L, int64_t T, const int64_t *mono_ptr, const int32_t *var,
+                const uint8_t *exp, const double *x, double *out) {
+  if (L != 1 && L != 2 && L != 4) return O_EINVAL;
+  const int64_t W = 2 * L;
+  for (int64_t t = 0; t < T; t++) {
+    double acc[8];
+    c_one(L, acc);
+    for (int64_t o = mono_ptr[t]; o < mono_ptr[t + 1]; o++)
+      for (int r = 0; r < exp[o]; r++) c_mul(L, acc, x + (int64_t)var[o] * W, acc);
+    memcpy(out + t * W, acc, sizeof(double) * W);
+  }
+  return O_OK;
+}
+
+int o_coef_grad(int L, int32_t N, const int64_t *poly_ptr, const double *lam,
+                const double *mono, double *grad) {
+  if (L != 1 && L != 2 && L != 4) return O_EINVAL;
+  const int64_t W = 2 * L;
+  for (int i = 0; i < N; i++)
+    for (int64_t t = poly_ptr[i]; t < poly_ptr[i + 1]; t++) {
+      c_conj_mul(L, mono + t * W, lam + (int64_t)i * W, grad + t * W);
+      for (int l = 0; l < W; l++) grad[t * W + l] = -grad[t * W + l];
+    }
   return O_OK;
 }
 

@@ -501,6 +501,8 @@ WORKLOADS = {
     "gn32": dict(N=32, n=32, M=32, k=9, dmax=3, steps=4, config=1),
     # plain Gauss-Newton at scale (D, DD, QD)
     "gn256": dict(N=256, n=256, M=256, k=16, dmax=5, steps=4, config=2),
+    # coefficient gradient at the converged root (complex DD)
+    "adj128": dict(N=128, n=128, M=128, k=12, dmax=3, steps=4, config=4),
 }
 
 BATCH_WORKLOADS = {

@@ -44,6 +44,21 @@ MUTANTS = [
     ("last limb dropped in rounding",
      "    out[l] = approx;\n    if (approx != 0.0) x_grow(e, -approx);",
      "    out[l] = (l == L - 1 && L > 1) ? 0.0 : approx;\n    if (approx != 0.0) x_grow(e, -approx);"),
+    ("no conjugate in the forward substitution with R^H",
+     "c_conj_mul(L, R + ((int64_t)l * ldr + j) * W, w + (int64_t)j * W, p);",
+     "c_mul(L, R + ((int64_t)l * ldr + j) * W, w + (int64_t)j * W, p);"),
+    ("R read untransposed in the forward substitution",
+     "c_conj_mul(L, R + ((int64_t)l * ldr + j) * W, w + (int64_t)j * W, p);",
+     "c_conj_mul(L, R + ((int64_t)j * ldr + l) * W, w + (int64_t)j * W, p);"),
+    ("lambda conjugated instead of the monomial",
+     "c_conj_mul(L, mono + t * W, lam + (int64_t)i * W, grad + t * W);",
+     "c_conj_mul(L, lam + (int64_t)i * W, mono + t * W, grad + t * W);"),
+    ("sign of the coefficient gradient",
+     "for (int l = 0; l < W; l++) grad[t * W + l] = -grad[t * W + l];",
+     "for (int l = 0; l < W; l++) grad[t * W + l] = grad[t * W + l];"),
+    ("exponent ignored in the monomial values",
+     "for (int r = 0; r < exp[o]; r++) c_mul(L, acc, x + (int64_t)var[o] * W, acc);",
+     "for (int r = 0; r < 1; r++) c_mul(L, acc, x + (int64_t)var[o] * W, acc);"),
     ("update subtracts instead of adds",
      "for (int i = 0; i < n; i++) c_add(L, x + i * W, dx + i * W, x + i * W);",
      "for (int i = 0; i < n; i++) c_sub(L, x + i * W, dx + i * W, x + i * W);"),
@@ -64,6 +79,7 @@ def test_pins_catch_mutant(name, old, new, tmp_path):
     r = subprocess.run(
         [sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
          "tests/test_oracle_arith.py", "tests/test_oracle_eval.py",
-         "tests/test_oracle_mgs.py", "tests/test_oracle_newton.py"],
+         "tests/test_oracle_mgs.py", "tests/test_oracle_newton.py",
+         "tests/test_oracle_adjoint.py"],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught the mutant: {name}\n{r.stdout[-2000:]}"
