@@ -178,6 +178,44 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
                     gn_report *report, void *cuda_stream);
 
 /*
+ * Replace the coefficients of a loaded system from device memory (the
+ * supports stay).  d_coef: [T][2][coef_limbs] doubles, the layout of
+ * gn_system_create's h_coef, caller-owned; coef_limbs 1, 2 or 4.  Stream-
+ * ordered: calls issued later on the same stream see the new coefficients,
+ * and captured Newton step graphs stay valid (they read the coefficients
+ * when they run).  Returns GN_EINVAL for a null system or pointer or an
+ * unknown coef_limbs.
+ */
+gn_status gn_system_set_coef(gn_system *s, const double *d_coef, int32_t coef_limbs,
+                             void *cuda_stream);
+
+/*
+ * Gradient of a real loss with respect to every coefficient at a root x.
+ * The paper's Newton's method (Section 4) is the forward solve; this is its
+ * adjoint by the implicit function theorem at the Gauss-Newton fixed point:
+ * at a root with J of full column rank the root moves by dx = -J^+ (df/dc) dc,
+ * J^+ = R^-1 Q^H for J = QR (Section 3), so for a loss gradient
+ * g = dL/dRe x + i dL/dIm x the coefficient gradient is
+ *   grad_t = dL/dRe c_t + i dL/dIm c_t = -lambda_i conj(x^{a_t}),
+ *   lambda = Q w with R^H w = g,
+ * for term t of polynomial i.  Every coefficient, constant terms included,
+ * counts as an independent input.
+ *   d_x      : [n] complex at precision prec, a root of the system (the
+ *              result of gn_newton); the formula is the derivative of the
+ *              root only where f(x) = 0.
+ *   d_g      : [n] complex, the loss gradient at x (2x for L = sum |x_j|^2).
+ *   d_grad   : [T] complex, output.
+ *   d_lambda : [N] complex, output, may be NULL.
+ * Evaluates [J, -f] at x (Section 2), factors it by MGS (Section 3) in the
+ * system's arithmetic, then solves R^H w = g, forms lambda = Q w and the
+ * gradients in the cascade arithmetic of precision prec.  Synchronizes the
+ * stream.  Returns GN_ESINGULAR for a rank-deficient J (the rank test of
+ * gn_lstsq), and then leaves d_grad and d_lambda undefined.
+ */
+gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, const double *d_g,
+                     double *d_grad, double *d_lambda, void *cuda_stream);
+
+/*
  * Batches: many independent square systems (N_s = n_s <= 128) advanced
  * together (Section 4 steps on every system of the batch).  The systems are
  * stored back to back in sparse distributed form (Section 1):

@@ -17,6 +17,7 @@ struct Workspace {
   double *Ab = nullptr;         // N x (n+1) complex, column-major, ld N
   double *R = nullptr;          // (n+1) x (n+1) complex, column-major
   double *dx = nullptr;         // [n] complex
+  double *lam = nullptr;        // [N] complex: multipliers of the coefficient gradient
   double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, [n+1] original column norms, [n+1] exponents
   double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
   int32_t *status = nullptr;    // sticky device status word

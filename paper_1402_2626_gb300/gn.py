@@ -34,7 +34,8 @@ REPORT_MAX = 64
 # exported symbols declared in include/gn.h
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
            "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_batch_create", "gn_batch_destroy",
-           "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc")
+           "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc",
+           "gn_system_set_coef", "gn_adjoint")
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
@@ -87,6 +88,10 @@ def load_library(path: str = LIB_PATH):
         L.gn_mgs.restype = C.c_int
         L.gn_newton.argtypes = [vp, C.c_int, vp, C.c_int32, dp, C.POINTER(Report), vp]
         L.gn_newton.restype = C.c_int
+        L.gn_system_set_coef.argtypes = [vp, vp, C.c_int32, vp]
+        L.gn_system_set_coef.restype = C.c_int
+        L.gn_adjoint.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+        L.gn_adjoint.restype = C.c_int
         L.gn_batch_create.argtypes = [C.POINTER(vp), C.c_int32, i64p, C.c_int64, i64p, i64p,
                                       C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
                                       C.POINTER(C.c_double), C.c_int32]
@@ -199,6 +204,20 @@ class System:
         _check(self._lib.gn_mgs(self._h, PREC[prec], m, ncols - 1, _ptr(Ab), m, _ptr(R),
                                 C.c_void_p(status.data_ptr()), _stream(stream)), "gn_mgs")
 
+    def set_coef(self, coef, stream=None):
+        """Replace the coefficients from a CUDA tensor [T,2,Lc] (Lc = 1, 2 or 4)."""
+        if coef.dim() != 3 or coef.shape[0] != self.T or coef.shape[1] != 2:
+            raise ValueError("coef must have shape [T, 2, limbs]")
+        _check(self._lib.gn_system_set_coef(self._h, _ptr(coef), coef.shape[2], _stream(stream)),
+               "gn_system_set_coef")
+
+    def adjoint(self, prec, x, g, grad, lam=None, stream=None):
+        """Coefficient gradient at the root x [n,2,L] for the loss gradient
+        g [n,2,L]: grad [T,2,L] (and lam [N,2,L] if given) are written;
+        synchronizes the stream."""
+        _check(self._lib.gn_adjoint(self._h, PREC[prec], _ptr(x), _ptr(g), _ptr(grad), _ptr(lam),
+                                    _stream(stream)), "gn_adjoint")
+
     def newton(self, prec, x, steps, tol=0.0, stream=None, raise_on_error=True):
         """``steps`` Gauss-Newton steps in place on x [n,2,L]; returns the report."""
         rep = Report()
@@ -264,3 +283,52 @@ class Batch:
         _check(self._lib.gn_batch_newton(self._h, PREC[prec], _ptr(x), steps, _ptr(norms),
                                          C.c_void_p(status.data_ptr()), _stream(stream)),
                "gn_batch_newton")
+
+
+_root_fn = None
+
+
+def _root_function():
+    global _root_fn
+    if _root_fn is None:
+        import torch
+
+        class NewtonRoot(torch.autograd.Function):
+            """x = root of the system with coefficients ``coef`` reached by
+            ``steps`` Gauss-Newton steps from x0 (gn_newton); the backward pass
+            is gn_adjoint at that root."""
+
+            @staticmethod
+            def forward(ctx, coef, system, prec, x0, steps):
+                system.set_coef(coef)
+                x = x0.detach().clone().contiguous()
+                system.newton(prec, x, steps)
+                ctx.save_for_backward(coef, x)
+                ctx.system, ctx.prec = system, prec
+                return x
+
+            @staticmethod
+            def backward(ctx, gx):
+                coef, x = ctx.saved_tensors
+                system, prec = ctx.system, ctx.prec
+                system.set_coef(coef)  # the system may hold other coefficients by now
+                # first order, a change of the root shows in its leading limb
+                g = torch.zeros_like(x)
+                g[..., 0] = gx[..., 0]
+                grad = torch.empty((system.T, 2, PREC[prec]), dtype=torch.float64, device=x.device)
+                system.adjoint(prec, x, g, grad)
+                # a coefficient's value is the sum of its limbs: each limb gets dL/dc
+                gc = grad[..., :1].expand(-1, -1, coef.shape[2]).contiguous()
+                return gc, None, None, None, None
+
+        _root_fn = NewtonRoot
+    return _root_fn
+
+
+def newton_root(system: System, prec, coef, x0, steps: int):
+    """Differentiable root: ``steps`` Gauss-Newton steps from x0 [n,2,L] on
+    ``system`` with its coefficients replaced by coef [T,2,Lc] (a CUDA
+    tensor that may require grad).  Backward gives dL/dcoef by the adjoint
+    (gn_adjoint); the loss gradient is taken from the leading limb of x, and
+    every limb of a coefficient receives the coefficient's gradient."""
+    return _root_function().apply(coef, system, prec, x0, steps)
