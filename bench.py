@@ -201,6 +201,21 @@ def cpu_baseline(system, L, budget_s=15.0):
                       f"{ {1: 'D', 2: 'DD', 4: 'QD'}[L]} ({sum(times):.1f} s)"}
 
 
+def cpu_adjoint_baseline():
+    """The oracle's coefficient gradient on the 128-variable workload (DD), at
+    its own root, timed on the host cores: about one second of CPU work."""
+    import oracle
+    from paper_1402_2626_gb300 import inputs
+
+    s = inputs.workload("adj128")
+    cores = os.cpu_count() or 1
+    x, _ = oracle.newton(s, s.point("x0", 2), 2, 4, nthreads=cores)
+    t = time.perf_counter()
+    oracle.adjoint(s, x, 2.0 * x, 2, nthreads=cores)
+    return {"gradient_ms": 1e3 * (time.perf_counter() - t), "cores": cores, "kind": "oracle",
+            "sample": "one coefficient gradient of the adj128 workload in DD"}
+
+
 def run_reference(args):
     """The CPU oracle on the same workload, metric and steps (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -328,6 +343,7 @@ def main():
     roofline = None
     if rank == 0 and not args.no_extras:
         extras, roofline = breakdown(S, system, dev, flush, args)
+        extras["adjoint"] = adjoint_extra(dev, flush, args)
         if not args.no_batch:
             extras["batched"] = batched(dev, args)
 
@@ -346,11 +362,65 @@ def main():
         }
         if not args.no_cpu:
             line["cpu_baseline"] = cpu_baseline(system, L)
+            if "adjoint" in line:
+                line["adjoint"]["cpu_baseline"] = cpu_adjoint_baseline()
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def adjoint_extra(dev, flush, args):
+    """The coefficient gradient at the converged root on the 128-variable
+    workload (N = n = 128, 128 terms of 12 variables per polynomial plus a
+    constant, exponents 1..3, complex DD): four Newton steps from x0, then
+    gn_adjoint (evaluation and MGS at the root, forward substitution with R^H,
+    lambda = Q w, one gradient per term).  Device events, L2 flushed first."""
+    import torch
+
+    from paper_1402_2626_gb300 import gn, inputs
+
+    s = inputs.workload("adj128")
+    L = 2
+    S = gn.System(s)
+    stream = torch.cuda.current_stream(dev)
+    x0 = torch.tensor(s.point("x0", L), device=dev)
+    x = x0.clone()
+    grad = torch.empty((s.T, 2, L), dtype=torch.float64, device=dev)
+    lam = torch.empty((s.N, 2, L), dtype=torch.float64, device=dev)
+    reps = max(5, min(args.steps, 20))
+
+    def timed(fn, prep):
+        for _ in range(2):
+            prep()
+            fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            prep()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    newton_ms = timed(lambda: S.newton("dd", x, 4), lambda: x.copy_(x0))
+    S.newton("dd", x, 4)
+    xr = x.clone()
+    g = 2.0 * xr
+    grad_ms = timed(lambda: S.adjoint("dd", xr, g, grad, lam), lambda: None)
+    # from the last Newton step's factorisation (the forward solve's own QR)
+    reuse_ms = timed(lambda: S.adjoint("dd", xr, g, grad, lam, reuse=True), lambda: None)
+    S.close()
+    return {"workload": "adj128", "N": s.N, "n": s.n, "T": s.T, "precision": "dd",
+            "newton_4_steps_ms": newton_ms, "gradient_ms": grad_ms,
+            "gradient_reuse_ms": reuse_ms,
+            "gradient_over_newton_step": grad_ms / (newton_ms / 4),
+            "gradients_per_s": s.T / (grad_ms / 1e3),
+            "loss": "sum |x_j|^2 at the root (g = 2x)"}
 
 
 def batched(dev, args, loop_sample=64):

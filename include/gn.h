@@ -206,14 +206,24 @@ gn_status gn_system_set_coef(gn_system *s, const double *d_coef, int32_t coef_li
  *   d_g      : [n] complex, the loss gradient at x (2x for L = sum |x_j|^2).
  *   d_grad   : [T] complex, output.
  *   d_lambda : [N] complex, output, may be NULL.
- * Evaluates [J, -f] at x (Section 2), factors it by MGS (Section 3) in the
- * system's arithmetic, then solves R^H w = g, forms lambda = Q w and the
- * gradients in the cascade arithmetic of precision prec.  Synchronizes the
- * stream.  Returns GN_ESINGULAR for a rank-deficient J (the rank test of
- * gn_lstsq), and then leaves d_grad and d_lambda undefined.
+ *   flags    : 0 evaluates [J, -f] at x (Section 2) and factors it by MGS
+ *              (Section 3) in the system's arithmetic; GN_ADJ_REUSE instead
+ *              takes the factorisation the last gn_newton (of J at the
+ *              iterate before its result) or gn_adjoint call at this
+ *              precision left, and returns GN_EINVAL when another call
+ *              (gn_lstsq, gn_mgs, gn_system_set_coef, gn_system_set_arith, a
+ *              failed step) has replaced it since.  After a converged run the
+ *              last step moved x by about the working precision, so the two
+ *              Jacobians agree to that precision; with a larger last step the
+ *              gradient is off by about that step's relative size.
+ * Then R^H w = g, lambda = Q w and the gradients follow in the cascade
+ * arithmetic of precision prec.  Synchronizes the stream.  Returns
+ * GN_ESINGULAR for a rank-deficient J (the rank test of gn_lstsq), and then
+ * leaves d_grad and d_lambda undefined.
  */
+#define GN_ADJ_REUSE 1
 gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, const double *d_g,
-                     double *d_grad, double *d_lambda, void *cuda_stream);
+                     double *d_grad, double *d_lambda, int32_t flags, void *cuda_stream);
 
 /*
  * Batches: many independent square systems (N_s = n_s <= 128) advanced

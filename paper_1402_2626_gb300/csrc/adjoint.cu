@@ -12,7 +12,7 @@
 // Three launches after the factorisation (evaluation and MGS are the Newton
 // step's own kernels, on [J, -f] at x):
 //   k_adj_fwdsub  R^H w = g by forward substitution (one CTA),
-//   k_adj_lambda  lambda = Q w (32 rows per CTA, 8 partial sums per row),
+//   k_adj_lambda  lambda = Q w (one CTA per row),
 //   k_adj_grad    grad_t = -lambda_i conj(x^{a_t}) (one thread per term).
 // The arithmetic is the cascade arithmetic of mw.cuh at precision L.
 #include "internal.h"
@@ -24,7 +24,10 @@ constexpr int ADJ_THREADS = 256;
 
 // w_l = (g_l - sum_{j<l} conj(r_jl) w_j) / r_ll for l = 0 .. n-1, column
 // oriented: once w_l is known every thread subtracts conj(r_li) w_l from its
-// w_i (i > l).  r_li is row l of R, entry (l, i) of the column-major factor.
+// w_i (i > l); r_li is row l of R, entry (l, i) of the column-major factor.
+// w_l itself is formed by one thread while the FP64 pipe is otherwise idle
+// (a lookahead that forms w_{l+1} during the updates measured slower: its
+// dependent chain then queues behind the other rows' updates).
 template <int L>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_fwdsub(const double *__restrict__ R, int64_t ldr,
                                                             int32_t n, const double *__restrict__ rinv,
@@ -55,32 +58,30 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_fwdsub(const double *__rest
   }
 }
 
-// lambda_i = sum_l q_il w_l.  Thread (r, c) of a CTA sums l = c, c+8, ...
-// for row i = 32 blockIdx.x + r; the 8 partial sums of a row are added in c
-// order, so the result does not depend on scheduling.
+// lambda_i = sum_l q_il w_l, one CTA per row: thread c sums l = c, c + 256,
+// ... and the partial sums meet in a fixed tree, so the result does not
+// depend on scheduling.
 template <int L>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_lambda(const double *__restrict__ Q, int64_t ldq,
                                                             int32_t m, int32_t n,
                                                             const double *__restrict__ w,
                                                             double *__restrict__ lam,
                                                             const int32_t *__restrict__ status) {
-  __shared__ cx<L> part[8][32];
+  __shared__ cx<L> part[ADJ_THREADS];
   if (*status != GN_OK) return;
   const int64_t W = 2 * L;
-  const int r = threadIdx.x & 31, c = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + r;
+  const int i = blockIdx.x;
   cx<L> acc = c_zero<L>();
-  if (i < m)
-    for (int l = c; l < n; l += 8)
-      acc = c_add<L>(acc, c_mul<L>(c_load<L>(Q + ((int64_t)l * ldq + i) * W), c_load<L>(w + l * W)));
-  part[c][r] = acc;
+  for (int l = threadIdx.x; l < n; l += ADJ_THREADS)
+    acc = c_add<L>(acc, c_mul<L>(c_load<L>(Q + ((int64_t)l * ldq + i) * W), c_load<L>(w + l * W)));
+  part[threadIdx.x] = acc;
   __syncthreads();
-  if (c == 0 && i < m) {
-    cx<L> s = part[0][r];
 #pragma unroll
-    for (int q = 1; q < 8; q++) s = c_add<L>(s, part[q][r]);
-    c_store<L>(lam + i * W, s);
+  for (int h = ADJ_THREADS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) part[threadIdx.x] = c_add<L>(part[threadIdx.x], part[threadIdx.x + h]);
+    __syncthreads();
   }
+  if (threadIdx.x == 0) c_store<L>(lam + i * W, part[0]);
 }
 
 // x^d by square and multiply (d >= 1)
@@ -145,8 +146,7 @@ static gn_status adjoint_tail(gn_system *s, Workspace *ws, const double *d_x, co
                               double *d_grad, double *lam, cudaStream_t st) {
   const int32_t N = s->N, n = s->n;
   k_adj_fwdsub<L><<<1, ADJ_THREADS, 0, st>>>(ws->R, n + 1, n, ws->rinv, d_g, ws->dx, ws->status);
-  k_adj_lambda<L><<<(unsigned)((N + 31) / 32), ADJ_THREADS, 0, st>>>(ws->Ab, N, N, n, ws->dx, lam,
-                                                                     ws->status);
+  k_adj_lambda<L><<<(unsigned)N, ADJ_THREADS, 0, st>>>(ws->Ab, N, N, n, ws->dx, lam, ws->status);
   if (s->T > 0)
     k_adj_grad<L><<<(unsigned)((s->T + 127) / 128), 128, 0, st>>>(
         s->T, N, s->d_poly_ptr, s->d_mono_off, s->d_occ, d_x, lam, d_grad, ws->status);
@@ -158,8 +158,9 @@ static gn_status adjoint_tail(gn_system *s, Workspace *ws, const double *d_x, co
 using namespace gn;
 
 extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, const double *d_g,
-                                double *d_grad, double *d_lambda, void *cuda_stream) {
-  if (!s || (prec != 1 && prec != 2 && prec != 4) || !d_x || !d_g || (s->T > 0 && !d_grad))
+                                double *d_grad, double *d_lambda, int32_t flags, void *cuda_stream) {
+  if (!s || (prec != 1 && prec != 2 && prec != 4) || !d_x || !d_g || (s->T > 0 && !d_grad) ||
+      (flags & ~GN_ADJ_REUSE))
     return GN_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Workspace *ws;
@@ -168,12 +169,23 @@ extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, c
   const int64_t W = 2 * prec;
   const int32_t N = s->N, n = s->n;
   double *lam = d_lambda ? d_lambda : ws->lam;
+  const bool reuse = (flags & GN_ADJ_REUSE) != 0;
+  if (reuse && ws->fact == 0) return GN_EINVAL;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  // [J, -f] at x and its factorisation, Q and R as cascades
-  e = launch_eval_sel(s, prec, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
-  if (!e)
-    e = launch_lstsq(s, prec, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
-                     ws->status, st, true);
+  if (reuse) {
+    // Q and R of the last Newton step: integer mantissas to cascades
+    if (ws->fact == 1) {
+      e = launch_mgs_to_cascade(prec, ws->Ab, N, N, n + 1, ws->rinv, ws->status, st);
+      if (!e) e = launch_mgs_r_out(prec, ws->R, ws->Rm, n + 1, n + 1, ws->rinv, ws->status, st);
+    }
+  } else {
+    // [J, -f] at x and its factorisation, Q and R as cascades
+    ws->fact = 0;
+    e = launch_eval_sel(s, prec, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
+    if (!e)
+      e = launch_lstsq(s, prec, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
+                       ws->status, st, true);
+  }
   if (!e) {
     switch (prec) {
       case 1: e = adjoint_tail<1>(s, ws, d_x, d_g, d_grad, lam, st); break;
@@ -186,6 +198,8 @@ extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, c
           cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess)
     return GN_ECUDA;
+  // Q and R are cascades now (the tail kernels leave them alone): reusable
+  ws->fact = ws->h_status[0] == GN_OK ? 2 : 0;
   return (gn_status)ws->h_status[0];
 }
 
@@ -193,6 +207,7 @@ extern "C" gn_status gn_system_set_coef(gn_system *s, const double *d_coef, int3
                                         void *cuda_stream) {
   if (!s || (coef_limbs != 1 && coef_limbs != 2 && coef_limbs != 4) || (s->T > 0 && !d_coef))
     return GN_EINVAL;
+  for (Workspace &w : s->ws) w.fact = 0;  // a factorisation of the old J
   if (s->T == 0) return GN_OK;
   k_set_coef<<<(unsigned)((s->T + 127) / 128), 128, 0, (cudaStream_t)cuda_stream>>>(
       s->T, d_coef, coef_limbs, s->d_coef);

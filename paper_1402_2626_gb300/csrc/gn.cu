@@ -254,6 +254,7 @@ gn_status gn_system_set_arith(gn_system *s, gn_arith arith) {
     return GN_EINVAL;
   if (s->arith == (int32_t)arith) return GN_OK;
   s->arith = arith;
+  for (Workspace &w : s->ws) w.fact = 0;
   for (Workspace &w : s->ws)
     if (w.step_exec) {
       cudaGraphExecDestroy(w.step_exec);
@@ -295,6 +296,7 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
     }
     own = true;
   }
+  ws->fact = 0;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
   e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, Rm, Zs, d_dx, ws->status, st, true);
   if (!e && cudaMemcpyAsync(ws->h_status, ws->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost,
@@ -320,6 +322,7 @@ gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
   Workspace *ws;
   gn_status e = workspace_get(s, prec, &ws);
   if (e) return e;
+  ws->fact = 0;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
   e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
                    ws->status, st, true);
@@ -388,6 +391,7 @@ extern "C" gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t 
     e = build_graph(s, prec, ws, d_x);
     if (e) return e;
   }
+  ws->fact = 0;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
   if (cudaMemsetAsync(ws->norms, 0, sizeof(double) * 3 * GN_REPORT_MAX, st) != cudaSuccess)
     return GN_ECUDA;
@@ -419,6 +423,8 @@ extern "C" gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t 
     return GN_ECUDA;
   run = (gn_status)ws->h_status[0];
   done = ws->h_status[1];
+  // the workspace now holds the factorisation of the last step's J
+  if (run == GN_OK && done >= 1) ws->fact = lstsq_int_path(s, prec, s->N, s->n) ? 1 : 2;
   if (run == GN_OK && tol > 0.0 && !converged) run = GN_ENOCONV;
   if (report) {
     memset(report, 0, sizeof(*report));

@@ -26,6 +26,9 @@ struct Workspace {
   double *Zs = nullptr;         // [(n+1) (L+1)] mantissas and exponents of 1/r_jj
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
+  // what Ab, R, Rm, Zs and rinv hold: 0 nothing reusable; 1 / 2 the
+  // factorisation of the last gn_newton step, integer mantissas / cascades
+  int fact = 0;
   // CUDA graph of one Newton step for a given x pointer and stream
   cudaGraphExec_t step_exec = nullptr;
   const double *graph_x = nullptr;
@@ -107,6 +110,8 @@ inline size_t stage_words(int L) { return 2 * (size_t)L + 1; }
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
                        double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q);
+// whether launch_lstsq takes the integer-mantissa path for an m x (n+1) [A b]
+bool lstsq_int_path(const gn_system *s, int L, int32_t m, int32_t n);
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                              const double *rinv, double *dx, int32_t *status, cudaStream_t st);
 constexpr int BACKSUB_INT_MAX_N = 1024;

@@ -279,6 +279,10 @@ static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
+bool lstsq_int_path(const gn_system *s, int L, int32_t m, int32_t n) {
+  return lstsq_int(s) && mgs_flow_clusters(L) > 0 && mgs_flow_fits(L, m, n + 1);
+}
+
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
                        double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q) {

@@ -39,6 +39,7 @@ SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_s
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
+ADJ_REUSE = 1  # gn_adjoint flag: reuse the last factorisation
 
 
 class GnError(RuntimeError):
@@ -90,7 +91,7 @@ def load_library(path: str = LIB_PATH):
         L.gn_newton.restype = C.c_int
         L.gn_system_set_coef.argtypes = [vp, vp, C.c_int32, vp]
         L.gn_system_set_coef.restype = C.c_int
-        L.gn_adjoint.argtypes = [vp, C.c_int, vp, vp, vp, vp, vp]
+        L.gn_adjoint.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int32, vp]
         L.gn_adjoint.restype = C.c_int
         L.gn_batch_create.argtypes = [C.POINTER(vp), C.c_int32, i64p, C.c_int64, i64p, i64p,
                                       C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
@@ -211,12 +212,13 @@ class System:
         _check(self._lib.gn_system_set_coef(self._h, _ptr(coef), coef.shape[2], _stream(stream)),
                "gn_system_set_coef")
 
-    def adjoint(self, prec, x, g, grad, lam=None, stream=None):
+    def adjoint(self, prec, x, g, grad, lam=None, reuse=False, stream=None):
         """Coefficient gradient at the root x [n,2,L] for the loss gradient
         g [n,2,L]: grad [T,2,L] (and lam [N,2,L] if given) are written;
-        synchronizes the stream."""
+        ``reuse`` takes the factorisation the last newton() or adjoint() left
+        (GN_ADJ_REUSE) instead of factoring J at x; synchronizes the stream."""
         _check(self._lib.gn_adjoint(self._h, PREC[prec], _ptr(x), _ptr(g), _ptr(grad), _ptr(lam),
-                                    _stream(stream)), "gn_adjoint")
+                                    ADJ_REUSE if reuse else 0, _stream(stream)), "gn_adjoint")
 
     def newton(self, prec, x, steps, tol=0.0, stream=None, raise_on_error=True):
         """``steps`` Gauss-Newton steps in place on x [n,2,L]; returns the report."""

@@ -83,5 +83,5 @@ def test_calls_reject_null_handles(lib):
     assert lib.gn_batch_newton(None, 2, None, 1, None, None, None) == 1
     assert lib.gn_batch_destroy(None) == 1
     assert lib.gn_batch_create(None, 1, None, 0, None, None, None, None, None, 1) == 1
-    assert lib.gn_adjoint(None, 2, None, None, None, None, None) == 1
+    assert lib.gn_adjoint(None, 2, None, None, None, None, 0, None) == 1
     assert lib.gn_system_set_coef(None, None, 2, None) == 1

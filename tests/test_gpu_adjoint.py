@@ -67,6 +67,39 @@ def test_adjoint_parity_small(name, kw, prec, L, arith):
     _check(lam, lam_o, L, "lambda")
 
 
+@pytest.mark.parametrize("arith", ["auto", "fp64"])
+@pytest.mark.parametrize("prec,L", PRECS)
+def test_adjoint_reuse_last_step(prec, L, arith):
+    """GN_ADJ_REUSE after a Newton step from a converged point: the gradient
+    at the new iterate from the step's own factorisation matches the oracle
+    (which factors J at that iterate); a second reuse gives the same; after
+    gn_system_set_coef there is nothing to reuse."""
+    gn = _gn()
+    name, kw = SMALL[1]
+    s = inputs.random_system(kw["N"], kw["n"], kw["M"], kw["k"], kw["dmax"], seed=kw["seed"])
+    x = _root(s, L)
+    sy = gn.System(s, arith=arith)
+    xd = torch.tensor(x, device="cuda")
+    sy.newton(prec, xd, 1)
+    gd = 2.0 * xd
+    grad = torch.zeros((s.T, 2, L), dtype=torch.float64, device="cuda")
+    lam = torch.zeros((s.N, 2, L), dtype=torch.float64, device="cuda")
+    sy.adjoint(prec, xd, gd, grad, lam, reuse=True)
+    g1 = grad.cpu().numpy()
+    xh = xd.cpu().numpy()
+    grad_o, lam_o = oracle.adjoint(s, xh, 2.0 * xh, L, nthreads=8)
+    _check(g1, grad_o, L, "grad")
+    _check(lam.cpu().numpy(), lam_o, L, "lambda")
+    grad.zero_()
+    sy.adjoint(prec, xd, gd, grad, reuse=True)
+    assert np.array_equal(grad.cpu().numpy(), g1)
+    sy.set_coef(torch.tensor(s.coef[:, :, :L], device="cuda"))
+    with pytest.raises(gn.GnError) as ei:
+        sy.adjoint(prec, xd, gd, grad, reuse=True)
+    assert ei.value.status == 1
+    sy.close()
+
+
 def test_adjoint_empty_polynomial():
     """A polynomial without terms (a zero row of J, lambda_i = 0) between
     others: the term-to-polynomial search must skip it."""
@@ -119,6 +152,12 @@ def test_adjoint_full_size_dd():
     grad_o, lam_o = oracle.adjoint(s, xh, 2.0 * xh, L, nthreads=16)
     _check(grad.cpu().numpy(), grad_o, L, "grad")
     _check(lam.cpu().numpy(), lam_o, L, "lambda")
+    # the factorisation of the last Newton step gives the same at DD accuracy
+    x.copy_(torch.tensor(s.point("x0", L), device="cuda"))
+    sy.newton("dd", x, 4)
+    assert np.array_equal(x.cpu().numpy(), xh)
+    sy.adjoint("dd", x, 2.0 * x, grad, lam, reuse=True)
+    _check(grad.cpu().numpy(), grad_o, L, "grad (reuse)")
     sy.close()
 
 
