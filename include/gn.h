@@ -178,6 +178,35 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
                     gn_report *report, void *cuda_stream);
 
 /*
+ * Gauss-Newton with the factorisation in double precision and the residuals
+ * at precision prec (GN_DD or GN_QD).  Section 5.2 of the paper finds the
+ * linear solve dominant when evaluation is cheap and suggests iterative
+ * methods in double arithmetic; this call is such a method:
+ *   1. d_steps Gauss-Newton steps (Section 4) in double precision on the
+ *      leading limbs of x (as gn_newton with GN_D);
+ *   2. refine_steps refinement steps with the last double factorisation
+ *      [J, -f] = Q R (Section 3) frozen: b = -f(x) at precision prec
+ *      (Section 2), y = Q^H b in double, R dx = y in double, x <- x + dx at
+ *      precision prec.
+ * Phase 2 gains about -log10(kappa(J) u_double) digits per step, so for a
+ * consistent system (f(x*) = 0) it reaches the root at precision prec:
+ * quad double from a double start takes three or four steps for
+ * kappa(J) up to about 1e4.
+ *   d_x          : [n] complex at precision prec, updated in place (after
+ *                  phase 1 its lower limbs are those of the double iterate).
+ *   d_steps      : >= 1; refine_steps >= 0; d_steps + refine_steps <= GN_REPORT_MAX.
+ *   tol          : 0 to take every refinement step; > 0 to stop the
+ *                  refinement once ||dx|| <= tol ||x|| (GN_ENOCONV if never).
+ *   report       : host-owned, may be NULL: the double steps first, then
+ *                  the refinement steps.
+ * Synchronizes the stream.  Returns GN_EINVAL for an unknown precision or
+ * step counts, and the status of phase 1 (GN_ESINGULAR, ...) if it fails.
+ * The paper has no counterpart of this entry point.
+ */
+gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, int32_t d_steps,
+                          int32_t refine_steps, double tol, gn_report *report, void *cuda_stream);
+
+/*
  * Replace the coefficients of a loaded system from device memory (the
  * supports stay).  d_coef: [T][2][coef_limbs] doubles, the layout of
  * gn_system_create's h_coef, caller-owned; coef_limbs 1, 2 or 4.  Stream-

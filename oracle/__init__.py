@@ -223,6 +223,54 @@ def newton(system, x0, L: int, steps: int, nthreads: int = 1):
     return x, hist
 
 
+# -- mixed precision: double factorisation, residuals at precision L --------------
+
+
+def newton_mixed(system, x0, L: int, d_steps: int, refine_steps: int, nthreads: int = 1):
+    """Gauss-Newton in two phases (an extension past the paper; Section 5.2
+    notes that the linear solve dominates a Newton step and that iterative
+    methods in double arithmetic may do well):
+
+    1. ``d_steps`` full Gauss-Newton steps (Section 4) in double precision from
+       the leading limbs of x0, keeping the factors Q, R of the last step's
+       [J, -f] (Section 3);
+    2. ``refine_steps`` refinement steps at precision L with those factors
+       frozen: b = -f(x) evaluated at precision L (Section 2) and rounded to
+       double, y = Q^H b in double (terms summed in row order), R dx = y by
+       back substitution in double, x <- x + dx at precision L.
+
+    Returns (x [n, 2, L], [(|f|_2, |dx|_2) per step]).
+    """
+    n = system.n
+    x = np.zeros((n, 2, 1))
+    x[:, :, 0] = np.asarray(x0)[:, :, 0]
+    hist = []
+    Q = R = None
+    for _ in range(d_steps):
+        f, J, _ = evaluate(system, x, 1, "reverse", nthreads=nthreads)
+        Q, R = mgs(augmented(f, J), 1, nthreads=nthreads)
+        dx = backsub(R, 1)
+        x = add_vec(x, dx, 1)
+        hist.append((float(np.sqrt((f[:, :, 0] ** 2).sum())), float(np.sqrt((dx[:, :, 0] ** 2).sum()))))
+    xl = np.zeros((n, 2, L))
+    xl[:, :, 0] = x[:, :, 0]
+    for _ in range(refine_steps):
+        f, _, _ = evaluate(system, xl, L, "reverse", jacobian=False, nthreads=nthreads)
+        b = -f[:, :, :1]
+        Ry = R.copy()
+        for k in range(n):
+            acc = np.zeros((2, 1))
+            for i in range(system.N):
+                acc = cplx_op(1, "add", acc, cplx_op(1, "conj_mul", Q[i, k], b[i]))
+            Ry[k, n] = acc
+        dx = backsub(Ry, 1)
+        dxl = np.zeros((n, 2, L))
+        dxl[:, :, 0] = dx[:, :, 0]
+        xl = add_vec(xl, dxl, L)
+        hist.append((float(np.sqrt((f[:, :, 0] ** 2).sum())), float(np.sqrt((dx[:, :, 0] ** 2).sum()))))
+    return xl, hist
+
+
 # -- adjoint (gradient with respect to the coefficients) ------------------------
 
 

@@ -42,6 +42,7 @@ static void ws_free(Workspace &w) {
   cudaFree(w.R);
   cudaFree(w.dx);
   cudaFree(w.lam);
+  cudaFree(w.xmix);
   cudaFree(w.rinv);
   cudaFree(w.norms);
   cudaFree(w.status);
@@ -68,6 +69,7 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   if (!e) e = dalloc(&w.R, W * (n + 1) * (n + 1));
   if (!e) e = dalloc(&w.dx, W * n);
   if (!e) e = dalloc(&w.lam, W * N);
+  if (!e) e = dalloc(&w.xmix, 2 * n);
   if (!e) e = dalloc(&w.rinv, lstsq_scratch_doubles(s->n, L));
   if (!e) e = dalloc(&w.norms, 3 * GN_REPORT_MAX);
   if (!e) e = dalloc(&w.status, 2);

@@ -18,6 +18,7 @@ struct Workspace {
   double *R = nullptr;          // (n+1) x (n+1) complex, column-major
   double *dx = nullptr;         // [n] complex
   double *lam = nullptr;        // [N] complex: multipliers of the coefficient gradient
+  double *xmix = nullptr;       // [n] complex: the double iterate of mixed-precision Newton
   double *rinv = nullptr;       // [(n+1) L] 1 / r_kk, [n+1] original column norms, [n+1] exponents
   double *norms = nullptr;      // [3 * GN_REPORT_MAX]: |f|, |dx|, |x| per step
   int32_t *status = nullptr;    // sticky device status word
@@ -131,6 +132,9 @@ gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncol
                           int64_t ldr, double *rinv, uint32_t *flags, int32_t *status, double *Rm,
                           double *Zs, cudaStream_t st);
 constexpr int MGS_FLAGS_PER_COLUMN = 8;
+// R[0:n,0:n] dx = R[0:n, n] in the cascade arithmetic (one CTA, 1/r_ll from rinv)
+gn_status launch_backsub_fp64(int L, const double *R, int64_t ldr, int32_t n, const double *rinv,
+                              double *dx, const int32_t *status, cudaStream_t st);
 gn_status launch_update(int L, int32_t n, double *d_x, const double *d_dx, const double *d_fnorm,
                         double *d_norms, int32_t *d_status, cudaStream_t st);
 

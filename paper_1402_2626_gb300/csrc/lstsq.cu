@@ -296,6 +296,17 @@ gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, 
   return GN_EINVAL;
 }
 
+gn_status launch_backsub_fp64(int L, const double *R, int64_t ldr, int32_t n, const double *rinv,
+                              double *dx, const int32_t *status, cudaStream_t st) {
+  switch (L) {
+    case 1: k_backsub<1><<<1, MGS_THREADS, 0, st>>>(R, ldr, n, rinv, dx, status); break;
+    case 2: k_backsub<2><<<1, MGS_THREADS, 0, st>>>(R, ldr, n, rinv, dx, status); break;
+    case 4: k_backsub<4><<<1, MGS_THREADS, 0, st>>>(R, ldr, n, rinv, dx, status); break;
+    default: return GN_EINVAL;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
 gn_status launch_update(int L, int32_t n, double *d_x, const double *d_dx, const double *d_fnorm,
                         double *d_norms, int32_t *d_status, cudaStream_t st) {
   switch (L) {

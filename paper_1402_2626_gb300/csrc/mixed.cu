@@ -1,0 +1,196 @@
+// mixed.cu — Gauss-Newton with the factorisation in double precision and the
+// residuals in double double or quad double.
+//
+// Section 5.2 of Verschelde & Yu observes that when evaluation is cheap the
+// linear solve dominates a Newton step, and that iterative methods in double
+// arithmetic may do well.  Here that becomes a two-phase solver:
+//   1. Gauss-Newton steps (Section 4) in double precision from the leading
+//      limbs of x: evaluation, MGS on [J, -f] and back substitution, each
+//      step one replay of the double-precision step graph;
+//   2. refinement at precision L with the last double factorisation frozen:
+//      b = -f(x) evaluated at precision L (Section 2), y = Q^H b in double,
+//      R dx = y by back substitution in double, x <- x + dx at precision L.
+// Phase 2 converges linearly, by about kappa(J) times the unit roundoff of
+// double per step, to the precision of the residuals; for a consistent
+// system this is the root at precision L.  The factorisation, the cost the
+// paper finds dominant, runs once per double step instead of once per step
+// at precision L.
+#include <string.h>
+
+#include "internal.h"
+#include "mw.cuh"
+
+namespace gn {
+
+constexpr int MIX_THREADS = 256;
+
+// leading limbs of x (precision L) into xd (double)
+template <int L>
+__global__ void k_mix_lead(int32_t n, const double *__restrict__ x, double *__restrict__ xd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  xd[2 * i] = x[(int64_t)i * 2 * L];
+  xd[2 * i + 1] = x[(int64_t)i * 2 * L + L];
+}
+
+// a double complex vector as a cascade of precision L (lower limbs 0)
+template <int L>
+__global__ void k_mix_spread(int32_t n, const double *__restrict__ xd, double *__restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double *o = x + (int64_t)i * 2 * L;
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    o[l] = l ? 0.0 : xd[2 * i];
+    o[L + l] = l ? 0.0 : xd[2 * i + 1];
+  }
+}
+
+// y_k = sum_i conj(q_ik) b_i in double, b = the leading limbs of -f (stored
+// at precision L), into column n of R (the place of y in the factor of
+// [A b]); one CTA per column k, partial sums over rows i = tid, tid + 256,
+// ... added in a fixed tree.  CTA 0 also forms ||f||_2 (leading limbs).
+template <int L>
+__global__ void __launch_bounds__(MIX_THREADS) k_mix_qhb(const double *__restrict__ Q, int64_t ldq,
+                                                         int32_t m, int32_t n,
+                                                         const double *__restrict__ negf,
+                                                         double *__restrict__ R, int64_t ldr,
+                                                         double *__restrict__ fnorm,
+                                                         const int32_t *__restrict__ status) {
+  __shared__ double sre[MIX_THREADS], sim[MIX_THREADS], sf[MIX_THREADS];
+  if (*status != GN_OK) return;
+  const int k = blockIdx.x;
+  double re = 0.0, im = 0.0, ff = 0.0;
+  for (int i = threadIdx.x; i < m; i += MIX_THREADS) {
+    const double qr = Q[((int64_t)k * ldq + i) * 2], qi = Q[((int64_t)k * ldq + i) * 2 + 1];
+    const double br = negf[(int64_t)i * 2 * L], bi = negf[(int64_t)i * 2 * L + L];
+    re = fma(qr, br, fma(qi, bi, re));
+    im = fma(qr, bi, fma(-qi, br, im));
+    ff = fma(br, br, fma(bi, bi, ff));
+  }
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  sf[threadIdx.x] = ff;
+  __syncthreads();
+#pragma unroll
+  for (int h = MIX_THREADS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sre[threadIdx.x] += sre[threadIdx.x + h];
+      sim[threadIdx.x] += sim[threadIdx.x + h];
+      sf[threadIdx.x] += sf[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    R[((int64_t)n * ldr + k) * 2] = sre[0];
+    R[((int64_t)n * ldr + k) * 2 + 1] = sim[0];
+    if (k == 0) *fnorm = sqrt(sf[0]);
+  }
+}
+
+template <int L>
+static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double *d_x, cudaStream_t st) {
+  const int32_t N = s->N, n = s->n;
+  const int64_t W = 2 * L;
+  double *negf = wL->Ab + (int64_t)n * N * W;
+  double *fnorm = wL->rinv;  // the refinement factors nothing at precision L
+  gn_status e = launch_eval_sel(s, L, d_x, negf, 1, nullptr, N, st);
+  if (e) return e;
+  k_mix_qhb<L><<<(unsigned)n, MIX_THREADS, 0, st>>>(w1->Ab, N, N, n, negf, w1->R, n + 1, fnorm,
+                                                    wL->status);
+  e = launch_backsub_fp64(1, w1->R, n + 1, n, w1->rinv, w1->dx, wL->status, st);
+  if (e) return e;
+  k_mix_spread<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, w1->dx, wL->dx);
+  return launch_update(L, n, d_x, wL->dx, fnorm, wL->norms, wL->status, st);
+}
+
+}  // namespace gn
+
+using namespace gn;
+
+extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, int32_t d_steps,
+                                     int32_t refine_steps, double tol, gn_report *report,
+                                     void *cuda_stream) {
+  if (!s || (prec != GN_DD && prec != GN_QD) || !d_x || d_steps < 1 || refine_steps < 0 ||
+      d_steps + refine_steps > GN_REPORT_MAX || !(tol >= 0.0))
+    return GN_EINVAL;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const int L = prec;
+  const int32_t n = s->n;
+  Workspace *w1, *wL;
+  gn_status e = workspace_get(s, 1, &w1);
+  if (!e) e = workspace_get(s, L, &wL);
+  if (e) return e;
+  if (report) memset(report, 0, sizeof(*report));
+  const unsigned nb = (unsigned)((n + 127) / 128);
+  // phase 1: double-precision Gauss-Newton on the leading limbs
+  switch (L) {
+    case 2: k_mix_lead<2><<<nb, 128, 0, st>>>(n, d_x, w1->xmix); break;
+    case 4: k_mix_lead<4><<<nb, 128, 0, st>>>(n, d_x, w1->xmix); break;
+  }
+  if (cudaPeekAtLastError() != cudaSuccess) return GN_ECUDA;
+  gn_report r1;
+  e = gn_newton(s, GN_D, w1->xmix, d_steps, 0.0, &r1, cuda_stream);
+  if (report) {
+    report->steps_done = r1.steps_done;
+    for (int k = 0; k < r1.steps_done; k++) {
+      report->res_norm[k] = r1.res_norm[k];
+      report->dx_norm[k] = r1.dx_norm[k];
+    }
+    report->status = e;
+  }
+  if (e) return e;
+  // the last step's factors as doubles
+  if (w1->fact == 1) {
+    e = launch_mgs_to_cascade(1, w1->Ab, s->N, s->N, n + 1, w1->rinv, w1->status, st);
+    if (!e) e = launch_mgs_r_out(1, w1->R, w1->Rm, n + 1, n + 1, w1->rinv, w1->status, st);
+    if (e) return e;
+    w1->fact = 2;
+  }
+  if (w1->fact != 2) return GN_EINVAL;
+  switch (L) {
+    case 2: k_mix_spread<2><<<nb, 128, 0, st>>>(n, w1->xmix, d_x); break;
+    case 4: k_mix_spread<4><<<nb, 128, 0, st>>>(n, w1->xmix, d_x); break;
+  }
+  // phase 2: refinement with frozen factors
+  wL->fact = 0;
+  if (cudaMemsetAsync(wL->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess ||
+      cudaMemsetAsync(wL->norms, 0, sizeof(double) * 3 * GN_REPORT_MAX, st) != cudaSuccess)
+    return GN_ECUDA;
+  bool converged = false;
+  for (int32_t k = 0; k < refine_steps; k++) {
+    e = L == 2 ? refine_step<2>(s, w1, wL, d_x, st) : refine_step<4>(s, w1, wL, d_x, st);
+    if (e) return e;
+    if (tol > 0.0) {
+      if (cudaMemcpyAsync(wL->h_status, wL->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(wL->h_norms, wL->norms, sizeof(double) * 3 * GN_REPORT_MAX,
+                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        return GN_ECUDA;
+      if (wL->h_status[0] != GN_OK) break;
+      if (wL->h_norms[3 * k + 1] <= tol * wL->h_norms[3 * k + 2]) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  if (cudaMemcpyAsync(wL->h_status, wL->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(wL->h_norms, wL->norms, sizeof(double) * 3 * GN_REPORT_MAX,
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GN_ECUDA;
+  gn_status run = (gn_status)wL->h_status[0];
+  const int32_t done = wL->h_status[1];
+  if (run == GN_OK && tol > 0.0 && !converged && refine_steps > 0) run = GN_ENOCONV;
+  if (report) {
+    report->status = run;
+    for (int32_t k = 0; k < done && r1.steps_done + k < GN_REPORT_MAX; k++) {
+      report->res_norm[r1.steps_done + k] = wL->h_norms[3 * k];
+      report->dx_norm[r1.steps_done + k] = wL->h_norms[3 * k + 1];
+    }
+    report->steps_done = r1.steps_done + done;
+  }
+  return run;
+}

@@ -35,7 +35,7 @@ REPORT_MAX = 64
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
            "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_batch_create", "gn_batch_destroy",
            "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc",
-           "gn_system_set_coef", "gn_adjoint")
+           "gn_system_set_coef", "gn_adjoint", "gn_newton_mixed")
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_system_set_coef.restype = C.c_int
         L.gn_adjoint.argtypes = [vp, C.c_int, vp, vp, vp, vp, C.c_int32, vp]
         L.gn_adjoint.restype = C.c_int
+        L.gn_newton_mixed.argtypes = [vp, C.c_int, vp, C.c_int32, C.c_int32, dp, C.POINTER(Report), vp]
+        L.gn_newton_mixed.restype = C.c_int
         L.gn_batch_create.argtypes = [C.POINTER(vp), C.c_int32, i64p, C.c_int64, i64p, i64p,
                                       C.POINTER(C.c_int32), C.POINTER(C.c_uint8),
                                       C.POINTER(C.c_double), C.c_int32]
@@ -230,6 +232,22 @@ class System:
                    dx_norm=list(rep.dx_norm[: rep.steps_done]))
         if raise_on_error and st != 0:
             raise GnError(st, "gn_newton")
+        return out
+
+
+    def newton_mixed(self, prec, x, d_steps, refine_steps, tol=0.0, stream=None,
+                     raise_on_error=True):
+        """Mixed-precision Gauss-Newton in place on x [n,2,L] (L = 2 or 4):
+        ``d_steps`` double-precision steps, then ``refine_steps`` refinement
+        steps with that factorisation and residuals at precision L."""
+        rep = Report()
+        st = self._lib.gn_newton_mixed(self._h, PREC[prec], _ptr(x), d_steps, refine_steps,
+                                       float(tol), C.byref(rep), _stream(stream))
+        out = dict(status=st, steps_done=rep.steps_done,
+                   res_norm=list(rep.res_norm[: rep.steps_done]),
+                   dx_norm=list(rep.dx_norm[: rep.steps_done]))
+        if raise_on_error and st != 0:
+            raise GnError(st, "gn_newton_mixed")
         return out
 
 

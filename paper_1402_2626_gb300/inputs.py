@@ -503,6 +503,9 @@ WORKLOADS = {
     "gn256": dict(N=256, n=256, M=256, k=16, dmax=5, steps=4, config=2),
     # coefficient gradient at the converged root (complex DD)
     "adj128": dict(N=128, n=128, M=128, k=12, dmax=3, steps=4, config=4),
+    # mixed precision: overdetermined and consistent, factorisation in double,
+    # residuals in quad double (63 terms plus the constant per polynomial)
+    "mix1536": dict(N=1536, n=1024, M=63, k=8, dmax=4, steps=4, config=5),
 }
 
 BATCH_WORKLOADS = {

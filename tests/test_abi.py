@@ -85,3 +85,4 @@ def test_calls_reject_null_handles(lib):
     assert lib.gn_batch_create(None, 1, None, 0, None, None, None, None, None, 1) == 1
     assert lib.gn_adjoint(None, 2, None, None, None, None, 0, None) == 1
     assert lib.gn_system_set_coef(None, None, 2, None) == 1
+    assert lib.gn_newton_mixed(None, 4, None, 3, 4, 0.0, None, None) == 1
