@@ -344,6 +344,7 @@ def main():
     if rank == 0 and not args.no_extras:
         extras, roofline = breakdown(S, system, dev, flush, args)
         extras["adjoint"] = adjoint_extra(dev, flush, args)
+        extras["mixed"] = mixed_extra(dev, flush, args)
         if not args.no_batch:
             extras["batched"] = batched(dev, args)
 
@@ -369,6 +370,62 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def mixed_extra(dev, flush, args):
+    """Time to a quad-double root on the mixed-precision workload (N = 1536
+    polynomials, n = 1024 variables, 63 terms of 8 variables plus a constant
+    per polynomial, exponents 1..4, consistent): gn_newton_mixed with two
+    double-precision steps and four QD refinement steps against four plain
+    QD Gauss-Newton steps (gn_newton), both from x0 = x* + 1e-6.  Device
+    events, L2 flushed first; the error of each result against the exact
+    root x* built into the system is reported beside its time."""
+    import numpy as np
+    import torch
+
+    from paper_1402_2626_gb300 import gn, inputs
+
+    s = inputs.workload("mix1536")
+    S = gn.System(s)
+    stream = torch.cuda.current_stream(dev)
+    x0 = torch.tensor(s.point("x0", 4), device=dev)
+    x = x0.clone()
+    xs = torch.zeros_like(x0)
+    xs[:, :, 0] = torch.tensor(s.xstar, device=dev)
+
+    def timed(fn, reps):
+        fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            x.copy_(x0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    def err():
+        d = (x - xs).cpu().numpy()
+        return float(np.abs(d[:, 0, :].sum(-1) + 1j * d[:, 1, :].sum(-1)).max())
+
+    D_STEPS, REFINE, QD_STEPS = 2, 4, 4
+    mixed_ms = timed(lambda: S.newton_mixed("qd", x, D_STEPS, REFINE), 3)
+    x.copy_(x0)
+    rep = S.newton_mixed("qd", x, D_STEPS, REFINE)
+    err_mixed = err()
+    plain_ms = timed(lambda: S.newton("qd", x, QD_STEPS), 2)
+    x.copy_(x0)
+    S.newton("qd", x, QD_STEPS)
+    err_plain = err()
+    S.close()
+    return {"workload": "mix1536", "N": s.N, "n": s.n, "T": s.T, "precision": "qd",
+            "mixed": {"double_steps": D_STEPS, "refine_steps": REFINE, "ms": mixed_ms,
+                      "err_vs_root": err_mixed, "dx_norms": rep["dx_norm"]},
+            "plain_qd": {"steps": QD_STEPS, "ms": plain_ms, "err_vs_root": err_plain},
+            "speedup_vs_plain_qd": plain_ms / mixed_ms}
 
 
 def adjoint_extra(dev, flush, args):

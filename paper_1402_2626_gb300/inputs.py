@@ -50,6 +50,9 @@ import numpy as np
 BASE_SEED = 0x14022626
 
 __all__ = [
+    "cyclic",
+    "cyclic_homotopy",
+    "chandrasekhar",
     "Batch",
     "random_batch",
     "batch_workload",
@@ -264,6 +267,147 @@ def _set_constants(s: System) -> None:
         for t in const_t[:1]:
             s.coef[t, 0, :] = cascade_from_fraction(re, 4)
             s.coef[t, 1, :] = cascade_from_fraction(im, 4)
+
+
+# -- the paper's closed-form benchmark systems ------------------------------------
+
+
+def _cyclic_windows(n: int, i: int) -> np.ndarray:
+    """Supports of polynomial i of cyclic n-roots: the n windows
+    {j, ..., j+i-1 mod n}, each sorted ascending ([n, i])."""
+    w = (np.arange(n)[:, None] + np.arange(i)[None, :]) % n
+    return np.sort(w, axis=1).astype(np.int32)
+
+
+def cyclic(n: int, seed: int = 0) -> System:
+    """The cyclic n-roots system (Section 5.3, eq. 7): for i = 1 .. n-1 the
+    sum over j = 0 .. n-1 of the products x_j x_{j+1} ... x_{j+i-1} (indices
+    mod n), and x_0 x_1 ... x_{n-1} - 1.  Coefficients 1 (and the constant
+    -1); every exponent 1.  ``x0`` is a seeded point of unit-modulus
+    coordinates (cos 2 pi u, sin 2 pi u), the kind of point the paper's
+    evaluation runs use; there is no built-in root (``xstar`` is None)."""
+    supports = [_cyclic_windows(n, i) for i in range(1, n)]
+    supports.append(np.arange(n, dtype=np.int32)[None, :])
+    poly_ptr = [0]
+    lengths = []
+    for i, w in enumerate(supports):
+        lengths.extend([w.shape[1]] * w.shape[0])
+        if i == n - 1:
+            lengths.append(0)  # the constant -1
+        poly_ptr.append(len(lengths))
+    mono_ptr = np.zeros(len(lengths) + 1, dtype=np.int64)
+    np.cumsum(lengths, out=mono_ptr[1:])
+    var = np.concatenate([w.ravel() for w in supports]).astype(np.int32)
+    T = len(lengths)
+    coef = np.zeros((T, 2, 4))
+    coef[:, 0, 0] = 1.0
+    coef[T - 1, 0, 0] = -1.0
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + 6000 + seed))
+    return System(N=n, n=n, poly_ptr=np.asarray(poly_ptr, dtype=np.int64), mono_ptr=mono_ptr,
+                  var=var, exp=np.ones(var.shape[0], dtype=np.uint8), coef=coef, xstar=None,
+                  x0=_unit(rng, n), name=f"cyclic{n}", meta=dict(n=n, seed=seed))
+
+
+def cyclic_homotopy(n: int, t: float = 1.0 - 2.0 ** -20, seed: int = 0) -> System:
+    """The Newton homotopy of Section 5.3 on cyclic n-roots: f(x) - t f(z) = 0,
+    which z solves at t = 1, with ``x0`` = z.  The paper draws z at random in
+    C^n; here z_k = i^(e_k) with e_k uniform in {0, 1, 2, 3}, so that every
+    product in f(z) is a power of i and f(z) is a Gaussian integer found by
+    counting, and t f(z) is exact in double (t = 1 - 2^-20 by default).  Each
+    polynomial gets the constant -t f_i(z) (the last one -1 - t f_n(z))."""
+    base = cyclic(n, seed)
+    rng = np.random.default_rng(np.random.SeedSequence(BASE_SEED + 7000 + seed))
+    e = rng.integers(0, 4, size=n)
+    pref = np.concatenate([[0], np.cumsum(np.concatenate([e, e]))])  # window sums via prefix sums
+    fz = []
+    for i in range(1, n):
+        pw = (pref[np.arange(n) + i] - pref[np.arange(n)]) % 4
+        cnt = np.bincount(pw, minlength=4)
+        fz.append((int(cnt[0] - cnt[2]), int(cnt[1] - cnt[3])))
+    q = int(e.sum()) % 4
+    prod_z = [(1, 0), (0, 1), (-1, 0), (0, -1)][q]
+    fz.append((prod_z[0] - 1, prod_z[1]))
+    poly_ptr = [0]
+    mono_ptr = [0]
+    coef_rows = []
+    for i in range(n):
+        t0, t1 = int(base.poly_ptr[i]), int(base.poly_ptr[i + 1])
+        last = i == n - 1
+        for tt in range(t0, t1 - (1 if last else 0)):
+            mono_ptr.append(int(base.mono_ptr[tt + 1]))
+            coef_rows.append((1.0, 0.0))
+        # constant: -t f_i(z), and for the last polynomial -1 - t f_n(z)
+        c = (-t * fz[i][0] - (1.0 if last else 0.0), -t * fz[i][1])
+        mono_ptr.append(mono_ptr[-1])
+        coef_rows.append(c)
+        poly_ptr.append(len(mono_ptr) - 1)
+    T = len(coef_rows)
+    coef = np.zeros((T, 2, 4))
+    coef[:, 0, 0] = [c[0] for c in coef_rows]
+    coef[:, 1, 0] = [c[1] for c in coef_rows]
+    z = np.stack([np.real(1j ** e), np.imag(1j ** e)], axis=-1).round()
+    return System(N=n, n=n, poly_ptr=np.asarray(poly_ptr, dtype=np.int64),
+                  mono_ptr=np.asarray(mono_ptr, dtype=np.int64), var=base.var, exp=base.exp,
+                  coef=coef, xstar=None, x0=z, name=f"cyclic{n}-homotopy",
+                  meta=dict(n=n, t=t, seed=seed, z_exponents=e))
+
+
+def _cascade_ratio(p: int, q: int, L: int) -> list[float]:
+    """Nearest-double cascade of the rational p/q (q > 0) with L limbs, in
+    integer arithmetic (CPython's int / int is correctly rounded)."""
+    out = []
+    num, den = p, q
+    for _ in range(L):
+        d = num / den if num else 0.0
+        out.append(d)
+        a, b = d.as_integer_ratio()  # d = a / b, b a power of two
+        num, den = num * b - a * den, den * b
+    return out
+
+
+def chandrasekhar(n: int, c: Fraction = Fraction(33, 64)) -> System:
+    """The Chandrasekhar H-equation system (Section 5.2, eq. 6), read with
+    j = 1 .. n (the equation prints j = 0 .. n-1 beside the 1-indexed H):
+    f_i = 2n H_i - c H_i sum_{j=1..n} (i / (i + j)) H_j - 2n, i = 1 .. n.
+    Terms of polynomial i: 2n H_i; -c i/(i+j) H_i H_j for j != i; -c/2 H_i^2;
+    the constant -2n.  Coefficients are rational: stored as the nearest
+    4-limb cascades.  ``x0`` is H = 1 (the paper's start); no built-in root."""
+    cn, cd = c.numerator, c.denominator
+    poly_ptr = [0]
+    mono_ptr = [0]
+    var = []
+    exp = []
+    coefs = []  # (p, q): the coefficient p / q
+    for i in range(1, n + 1):
+        # linear term
+        var.append(i - 1)
+        exp.append(1)
+        mono_ptr.append(len(var))
+        coefs.append((2 * n, 1))
+        for j in range(1, n + 1):
+            if j == i:
+                var.append(i - 1)
+                exp.append(2)
+            else:
+                a, b = (i - 1, j - 1) if i < j else (j - 1, i - 1)
+                var.append(a)
+                var.append(b)
+                exp.append(1)
+                exp.append(1)
+            coefs.append((-cn * i, cd * (i + j)))  # j = i: -c i / 2i = -c/2
+            mono_ptr.append(len(var))
+        mono_ptr.append(len(var))  # constant
+        coefs.append((-2 * n, 1))
+        poly_ptr.append(len(mono_ptr) - 1)
+    T = len(coefs)
+    coef = np.zeros((T, 2, 4))
+    for t, (pq, qq) in enumerate(coefs):
+        coef[t, 0, :] = _cascade_ratio(pq, qq, 4)
+    return System(N=n, n=n, poly_ptr=np.asarray(poly_ptr, dtype=np.int64),
+                  mono_ptr=np.asarray(mono_ptr, dtype=np.int64), var=np.asarray(var, dtype=np.int32),
+                  exp=np.asarray(exp, dtype=np.uint8), coef=coef, xstar=None,
+                  x0=np.stack([np.ones(n), np.zeros(n)], axis=-1), name=f"chandrasekhar{n}",
+                  meta=dict(n=n, c=str(c)))
 
 
 # -- batches of independent systems --------------------------------------------
