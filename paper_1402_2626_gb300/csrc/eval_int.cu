@@ -77,6 +77,7 @@ __global__ void __launch_bounds__(128) k_monomials_cf(
   if (t >= T || *status != GN_OK) return;
   const int o0 = __ldg(mono_off + t);
   const int k = __ldg(mono_off + t + 1) - o0;
+  if (k > KM) return;  // a long support: k_monomials_long_cf
   double cre[L], cim[L];
 #pragma unroll
   for (int l = 0; l < L; l++) {
@@ -107,6 +108,139 @@ __global__ void __launch_bounds__(128) k_monomials_cf(
     uint32_t w = __ldg(occ + o0 + s);
     cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_int<L>(cf_mul<L>(F[s], B), w & 255u));
     if (s > 0) B = cf_mul<L>(B, cf_ld<L>(pow + (int64_t)(w >> 8) * WS));
+  }
+}
+
+// a cf<K> value and whether it holds anything (the empty product)
+template <int K>
+struct cfo {
+  cf<K> v;
+  int has;
+};
+
+template <int K>
+__device__ __forceinline__ cfo<K> cfo_mul(const cfo<K> &a, const cfo<K> &b) {
+  if (!a.has) return b;
+  if (!b.has) return a;
+  return {cf_mul<K>(a.v, b.v), 1};
+}
+
+template <int K>
+__device__ __forceinline__ cfo<K> cfo_shfl(const cfo<K> &a, int src, int mode /* 0 idx, 1 up, 2 down */,
+                                           int delta) {
+  cfo<K> r;
+  auto sh = [&](uint64_t w) -> uint64_t {
+    return mode == 0 ? __shfl_sync(0xffffffffu, (unsigned long long)w, src)
+           : mode == 1 ? __shfl_up_sync(0xffffffffu, (unsigned long long)w, delta)
+                       : __shfl_down_sync(0xffffffffu, (unsigned long long)w, delta);
+  };
+  auto shi = [&](int w) -> int {
+    return mode == 0 ? __shfl_sync(0xffffffffu, w, src)
+           : mode == 1 ? __shfl_up_sync(0xffffffffu, w, delta)
+                       : __shfl_down_sync(0xffffffffu, w, delta);
+  };
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    r.v.re.w[w] = sh(a.v.re.w[w]);
+    r.v.im.w[w] = sh(a.v.im.w[w]);
+  }
+  r.v.e = shi(a.v.e);
+  r.has = shi(a.has);
+  return r;
+}
+
+// a staged value written by this thread earlier in the launch (not __ldg:
+// the read-only path need not see this launch's own stores)
+template <int K>
+__device__ __forceinline__ cf<K> cf_ld_own(const double *p) {
+  const uint64_t *q = (const uint64_t *)p;
+  cf<K> z;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    z.re.w[w] = q[w];
+    z.im.w[w] = q[K + w];
+  }
+  z.e = (int)(int64_t)q[2 * K];
+  return z;
+}
+
+// Terms whose support is longer than KMAXI: one warp per term, the
+// Speelpenning product and gradient of Section 2.2 split over the lanes.
+// Lane l owns the support positions [l c, l c + c), c = ceil(k / 32), and
+// forms the product of its x's; two warp scans give every lane the product
+// of the lanes before it (E) and after it (S); then, within the chunk,
+//   left_s  = a E  prod_{r < s in chunk} x_r   (forward, parked in stage_d)
+//   right_s = prod_{r > s in chunk} x_r  S     (backward, running)
+// and stage_d[s] = d_s left_s right_s, stage_val = a prod_all x.  The
+// coefficient times the common factor prod x^(d-1) (Section 2.1), a, is the
+// product of lane partials reduced to lane 0 in a fixed tree.  The cyclic
+// n-roots system of Section 5.3 has supports up to n.
+template <int L>
+__global__ void __launch_bounds__(128) k_monomials_long_cf(
+    const int32_t *__restrict__ long_terms, int64_t nlong, const int32_t *__restrict__ mono_off,
+    const uint32_t *__restrict__ occ, const double *__restrict__ coef, int64_t T,
+    const double *__restrict__ pow, int32_t n, double *__restrict__ stage_val,
+    double *__restrict__ stage_d, const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (wid >= nlong || *status != GN_OK) return;  // uniform across the warp
+  const int64_t t = __ldg(long_terms + wid);
+  const int o0 = __ldg(mono_off + t);
+  const int k = __ldg(mono_off + t + 1) - o0;
+  const int c = (k + 31) >> 5;
+  const int s0 = lane * c < k ? lane * c : k;
+  const int s1 = s0 + c < k ? s0 + c : k;
+  // a = coefficient x common factor
+  cfo<L> a = {cf_zero<L>(), 0};
+  if (lane == 0) {
+    double cre[L], cim[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+      cre[l] = __ldg(coef + (int64_t)(2 * l + 0) * T + t);
+      cim[l] = __ldg(coef + (int64_t)(2 * l + 1) * T + t);
+    }
+    a = {cf_from_cascade<L, L>(cre, cim), 1};
+  }
+  cfo<L> p = {cf_zero<L>(), 0};
+  for (int s = s0; s < s1; s++) {
+    const uint32_t w = __ldg(occ + o0 + s);
+    const int d = (int)(w & 255u);
+    if (d >= 2) a = cfo_mul<L>(a, {cf_ld<L>(pow + ((int64_t)(d - 2) * n + (w >> 8)) * WS), 1});
+    p = cfo_mul<L>(p, {cf_ld<L>(pow + (int64_t)(w >> 8) * WS), 1});
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const cfo<L> u = cfo_shfl<L>(a, 0, 2, off);
+    if (lane < off) a = cfo_mul<L>(a, u);
+  }
+  a = cfo_shfl<L>(a, 0, 0, 0);
+  // inclusive prefix and suffix products of the lane partials
+  cfo<L> pre = p, suf = p;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const cfo<L> u = cfo_shfl<L>(pre, 0, 1, off);
+    const cfo<L> v = cfo_shfl<L>(suf, 0, 2, off);
+    if (lane >= off) pre = cfo_mul<L>(u, pre);
+    if (lane + off < 32) suf = cfo_mul<L>(suf, v);
+  }
+  const cfo<L> total = cfo_shfl<L>(pre, 31, 0, 0);
+  cfo<L> E = cfo_shfl<L>(pre, 0, 1, 1);
+  cfo<L> S = cfo_shfl<L>(suf, 0, 2, 1);
+  if (lane == 0) E.has = 0;
+  if (lane == 31) S.has = 0;
+  if (lane == 0) cf_st<L>(stage_val + t * WS, cfo_mul<L>(a, total).v);
+  cfo<L> left = cfo_mul<L>(a, E);
+  for (int s = s0; s < s1; s++) {
+    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, left.v);
+    left = cfo_mul<L>(left, {cf_ld<L>(pow + (int64_t)(__ldg(occ + o0 + s) >> 8) * WS), 1});
+  }
+  cfo<L> right = S;
+  for (int s = s1 - 1; s >= s0; s--) {
+    const uint32_t w = __ldg(occ + o0 + s);
+    const cfo<L> g = cfo_mul<L>({cf_ld_own<L>(stage_d + (int64_t)(o0 + s) * WS), 1}, right);
+    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_int<L>(g.v, w & 255u));
+    right = cfo_mul<L>(right, {cf_ld<L>(pow + (int64_t)(w >> 8) * WS), 1});
   }
 }
 
@@ -232,6 +366,10 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
       k_monomials_cf<L, KMAXI><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
           a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
   }
+  if (a.nlong > 0)
+    k_monomials_long_cf<L><<<(unsigned)((a.nlong + 3) / 4), 128, 0, st>>>(
+        a.long_terms, a.nlong, a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val,
+        a.stage_d, a.status);
   if (a.J && a.nz > 0)
     k_sum_jacobian_cf<L><<<(unsigned)((a.nz + 127) / 128), 128, 0, st>>>(
         a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
@@ -242,7 +380,7 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
 }
 
 gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st) {
-  if (a.kmax > KMAXI) return GN_EINVAL;
+  if (a.kmax > KMAXI && !a.long_terms) return GN_EINVAL;
   switch (L) {
     case 1: return eval_int_raw<1>(a, st);
     case 2: return eval_int_raw<2>(a, st);
@@ -253,7 +391,6 @@ gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st) {
 
 gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, int neg_f,
                           double *d_J, int64_t ldJ, cudaStream_t st) {
-  if (s->kmax > KMAXI) return GN_EINVAL;
   Workspace *ws;
   gn_status e = workspace_get(s, L, &ws);
   if (e) return e;
@@ -267,6 +404,8 @@ gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, i
   a.nvar = s->n;
   a.pmax = s->pmax;
   a.kmax = s->kmax;
+  a.long_terms = s->d_long;
+  a.nlong = s->nlong;
   a.pow = ws->pow;
   a.T = s->T;
   a.mono_off = s->d_mono_off;

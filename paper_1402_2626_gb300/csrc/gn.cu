@@ -201,6 +201,13 @@ gn_status gn_system_create(gn_system **out, int32_t N, int32_t n, int64_t T,
   if (!e) e = upload(&s->d_mono_off, mono_off.data(), mono_off.size());
   if (!e) e = upload(&s->d_occ, occ.data(), occ.size());
   if (!e) e = upload(&s->d_coef, coef.data(), coef.size());
+  {
+    std::vector<int32_t> lt;
+    for (int64_t t = 0; t < T; t++)
+      if (h_mono_ptr[t + 1] - h_mono_ptr[t] > 64) lt.push_back((int32_t)t);
+    s->nlong = (int64_t)lt.size();
+    if (!e && !lt.empty()) e = upload(&s->d_long, lt.data(), lt.size());
+  }
   if (!e) e = upload(&s->d_jz_row, jz_row.data(), jz_row.size());
   if (!e) e = upload(&s->d_jz_col, jz_col.data(), jz_col.size());
   if (!e) e = upload(&s->d_jz_ptr, jz_ptr.data(), jz_ptr.size());
@@ -221,6 +228,7 @@ gn_status gn_system_destroy(gn_system *s) {
   cudaFree(s->d_mono_off);
   cudaFree(s->d_occ);
   cudaFree(s->d_coef);
+  cudaFree(s->d_long);
   cudaFree(s->d_jz_row);
   cudaFree(s->d_jz_col);
   cudaFree(s->d_jz_ptr);

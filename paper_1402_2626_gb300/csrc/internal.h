@@ -47,6 +47,8 @@ struct gn_system {
   int32_t *d_mono_off = nullptr;  // [T+1] occurrence offsets
   uint32_t *d_occ = nullptr;      // [nnz] (var << 8) | exp
   double *d_coef = nullptr;       // [4 limbs][2 parts][T] limb-planar coefficients
+  int32_t *d_long = nullptr;      // [nlong] terms with more than 64 variables
+  int64_t nlong = 0;
   // Jacobian pattern in column-major order (by column, then row)
   int64_t nz = 0;
   int32_t *d_jz_row = nullptr;  // [nz]
@@ -76,6 +78,8 @@ struct EvalArgs {
   const int32_t *mono_off = nullptr;
   const uint32_t *occ = nullptr;  // (variable << 8) | exponent, variables in [0, nvar)
   const double *coef = nullptr;   // [4][2][T]
+  const int32_t *long_terms = nullptr;  // terms with supports longer than 64 (one warp each)
+  int64_t nlong = 0;
   int64_t nz = 0;
   const int32_t *jz_row = nullptr, *jz_col = nullptr, *jz_ptr = nullptr, *jz_occ = nullptr;
   const int64_t *jz_out = nullptr;  // complex-entry offsets of the J entries (or null: col ldJ + row)
@@ -91,8 +95,9 @@ struct EvalArgs {
 gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st);
 // whether the system's arithmetic evaluates (eval_int) or solves (lstsq) on
 // integer mantissas at precision L
+// (supports longer than 64 variables evaluate on integer mantissas always)
 inline bool eval_int(const gn_system *s, int L) {
-  return s->arith == GN_ARITH_INT || (s->arith == GN_ARITH_AUTO && L > 1);
+  return s->kmax > 64 || s->arith == GN_ARITH_INT || (s->arith == GN_ARITH_AUTO && L > 1);
 }
 inline bool lstsq_int(const gn_system *s) { return s->arith != GN_ARITH_FP64; }
 // the evaluation the system's arithmetic selects
