@@ -216,6 +216,24 @@ def cpu_adjoint_baseline():
             "sample": "one coefficient gradient of the adj128 workload in DD"}
 
 
+def run_section(args):
+    """One extra section alone (``--only``), e.g. under a profiler."""
+    import torch
+
+    from paper_1402_2626_gb300 import build
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    build.build()
+    flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
+    fn = {"adjoint": lambda: adjoint_extra(dev, flush, args),
+          "mixed": lambda: mixed_extra(dev, flush, args),
+          "paper": lambda: paper_extra(dev, flush, args),
+          "batched": lambda: batched(dev, args)}[args.only]
+    print(json.dumps({"section": args.only, args.only: fn()}), flush=True)
+    return 0
+
+
 def run_reference(args):
     """The CPU oracle on the same workload, metric and steps (rank 0 only)."""
     rank = int(os.environ.get("RANK", "0"))
@@ -258,9 +276,13 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip per-precision breakdowns")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
+    ap.add_argument("--only", choices=["adjoint", "mixed", "paper", "batched"],
+                    help="run one extra section alone and print it as the JSON line (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_section(args)
 
     import torch
 
@@ -345,6 +367,7 @@ def main():
         extras, roofline = breakdown(S, system, dev, flush, args)
         extras["adjoint"] = adjoint_extra(dev, flush, args)
         extras["mixed"] = mixed_extra(dev, flush, args)
+        extras["paper_workloads"] = paper_extra(dev, flush, args)
         if not args.no_batch:
             extras["batched"] = batched(dev, args)
 
@@ -372,11 +395,83 @@ def main():
     return 0
 
 
+# Table 5 of the paper: evaluation and differentiation of cyclic n-roots on
+# one NVIDIA K20C, ms (context only: another GPU, another decade)
+PAPER_CYCLIC_MS = {"d": {128: 1.13, 256: 6.97, 384: 21.59, 448: 32.68, 512: 46.43},
+                   "dd": {128: 6.45, 256: 37.15, 384: 120.48, 448: 182.19, 512: 267.39},
+                   "qd": {128: 29.45, 256: 152.82, 384: 513.78, 448: 809.15}}
+
+
+def paper_extra(dev, flush, args):
+    """The paper's own benchmark systems (Section 5): evaluation and
+    differentiation of cyclic n-roots at the sizes of Table 5 in D, DD and QD
+    (gn_eval, f and the full Jacobian), seven DD Newton iterations on the
+    homotopy f(x) - t f(z) of cyclic 512-roots from z, and six DD Newton
+    iterations on the Chandrasekhar H-equation (c = 33/64, H = 1) at n = 1024
+    (Table 3's first size).  Device events, L2 flushed first."""
+    import torch
+
+    from paper_1402_2626_gb300 import gn, inputs
+
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps, prep=None):
+        if prep:
+            prep()
+        fn()
+        ms = []
+        for _ in range(reps):
+            flush.zero_()
+            if prep:
+                prep()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    out = {"cyclic_eval_diff_ms": {}, "paper_k20c_ms": PAPER_CYCLIC_MS}
+    for n in (128, 256, 384, 448, 512):
+        s = inputs.cyclic(n, seed=1)
+        S = gn.System(s)
+        row = {}
+        for prec, L in PRECS.items():
+            x = torch.tensor(s.point("x0", L), device=dev)
+            f = torch.empty((s.N, 2, L), dtype=torch.float64, device=dev)
+            J = torch.empty((s.n, s.N, 2, L), dtype=torch.float64, device=dev)
+            row[prec] = timed(lambda: S.eval(prec, x, f, J), 3)
+        out["cyclic_eval_diff_ms"][n] = row
+        S.close()
+    s = inputs.cyclic_homotopy(512)
+    S = gn.System(s)
+    x0 = torch.tensor(s.point("x0", 2), device=dev)
+    x = x0.clone()
+    ms = timed(lambda: S.newton("dd", x, 7), 3, lambda: x.copy_(x0))
+    x.copy_(x0)
+    rep = S.newton("dd", x, 7)
+    out["cyclic512_homotopy_dd_7_iterations"] = {"ms": ms, "dx_norms": rep["dx_norm"],
+                                                 "paper_k20c_s": 5930.96}
+    S.close()
+    s = inputs.chandrasekhar(1024)
+    S = gn.System(s)
+    x0 = torch.tensor(s.point("x0", 2), device=dev)
+    x = x0.clone()
+    ms = timed(lambda: S.newton("dd", x, 6), 2, lambda: x.copy_(x0))
+    x.copy_(x0)
+    rep = S.newton("dd", x, 6)
+    out["chandrasekhar1024_dd_6_iterations"] = {"ms": ms, "dx_norms": rep["dx_norm"],
+                                                "paper_k20c_gpu2_s": 20.083, "paper_cpu_s": 322.360}
+    S.close()
+    return out
+
+
 def mixed_extra(dev, flush, args):
     """Time to a quad-double root on the mixed-precision workload (N = 1536
     polynomials, n = 1024 variables, 63 terms of 8 variables plus a constant
     per polynomial, exponents 1..4, consistent): gn_newton_mixed with two
-    double-precision steps and four QD refinement steps against four plain
+    double-precision steps and six QD refinement steps against four plain
     QD Gauss-Newton steps (gn_newton), both from x0 = x* + 1e-6.  Device
     events, L2 flushed first; the error of each result against the exact
     root x* built into the system is reported beside its time."""
@@ -411,7 +506,9 @@ def mixed_extra(dev, flush, args):
         d = (x - xs).cpu().numpy()
         return float(np.abs(d[:, 0, :].sum(-1) + 1j * d[:, 1, :].sum(-1)).max())
 
-    D_STEPS, REFINE, QD_STEPS = 2, 4, 4
+    # two double steps leave the frozen Jacobian about 1e-10 from J(x*), so
+    # each refinement step gains about ten digits: six reach the QD floor
+    D_STEPS, REFINE, QD_STEPS = 2, 6, 4
     mixed_ms = timed(lambda: S.newton_mixed("qd", x, D_STEPS, REFINE), 3)
     x.copy_(x0)
     rep = S.newton_mixed("qd", x, D_STEPS, REFINE)
