@@ -184,7 +184,7 @@ extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, c
     e = launch_eval_sel(s, prec, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
     if (!e)
       e = launch_lstsq(s, prec, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
-                       ws->status, st, true);
+                       nullptr, ws->status, st, true);
   }
   if (!e) {
     switch (prec) {

@@ -1,0 +1,276 @@
+// bsb.cuh — blocked back substitution R x = y (Section 3, eq. 5) on the
+// integer mantissas MGS leaves, with explicit inverses of the diagonal
+// blocks.
+//
+// Solving one unknown at a time makes every level of the n-level chain a
+// dependent multi-word product, a reciprocal scaling and a barrier (about
+// 2 us per level in DD).  Here R is cut into BSB x BSB diagonal blocks D_k:
+//   k_bs_inv        X_k = D_k^-1 for every block at once (one warp per block,
+//                   lane c forms column c by substitution inside the block);
+//   k_backsub_blk   for k = last .. 0: x_k = X_k y_k, then y_i -= R_ik x_k for
+//                   the rows above (the rows of block k-1 first).
+// Both steps of a block are small matrix-vector products: every thread forms
+// one product and 16 lanes add theirs exactly (integer sums), so a block
+// costs two products and two 4-level reductions on the chain instead of 16
+// levels.  The formats are those of bs.cuh: y fixed point at the scale of
+// the last column with two limbs of headroom, x_l = X 2^t with K-limb X.
+// Entries of X_k are complex values with one binary exponent (cf.cuh).
+#pragma once
+
+#include "bs.cuh"
+#include "cf.cuh"
+#include "internal.h"
+
+namespace gn {
+
+constexpr int BSB = 16;              // block size
+constexpr int BSB_THREADS = 512;     // threads of the solve (32 rows x 16 columns per pass)
+
+// a complex value with N-limb integer parts at 2^e0 as cf<K>
+template <int K, int N>
+__device__ __forceinline__ cf<K> cf_from_fixed(const fx<N> &re, const fx<N> &im, int e0) {
+  const int b1 = ix_bitlen<N>(ix_abs_fx<N>(re)), b2 = ix_bitlen<N>(ix_abs_fx<N>(im));
+  const int B = b1 > b2 ? b1 : b2;
+  cf<K> z;
+  if (B == 0) return cf_zero<K>();
+  const int sh = B - (64 * K - 2);
+  fx<N> r = re, i = im;
+  if (sh > 0) {
+    r = ix_sar<N>(r, sh);
+    i = ix_sar<N>(i, sh);
+  } else if (sh < 0) {
+    r = ix_shl<N>(r, -sh);
+    i = ix_shl<N>(i, -sh);
+  }
+  z.re = ix_low<K, N>(r);
+  z.im = ix_low<K, N>(i);
+  z.e = e0 + sh;
+  return z;
+}
+
+template <int K>
+__device__ __forceinline__ cf<K> cf_neg(const cf<K> &a) {
+  cf<K> r = a;
+  fx<K> z;
+  fx_zero<K>(z);
+  r.re = ix_sub<K>(z, a.re);
+  r.im = ix_sub<K>(z, a.im);
+  return r;
+}
+
+template <int K>
+__device__ __forceinline__ void cf_put(double *p, const cf<K> &z) {
+  uint64_t *q = (uint64_t *)p;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    q[w] = z.re.w[w];
+    q[K + w] = z.im.w[w];
+  }
+  q[2 * K] = (uint64_t)(int64_t)z.e;
+}
+
+template <int K>
+__device__ __forceinline__ cf<K> cf_get(const double *p) {
+  const uint64_t *q = (const uint64_t *)p;
+  cf<K> z;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    z.re.w[w] = q[w];
+    z.im.w[w] = q[K + w];
+  }
+  z.e = (int)(int64_t)q[2 * K];
+  return z;
+}
+
+// exact sum of up to 16 cf values (lanes of one 16-lane group; inactive
+// lanes pass has = false), as cf<K> in every lane of the group
+template <int K>
+__device__ __forceinline__ cf<K> cf_group16_sum(const cf<K> &v, bool has) {
+  int e = has ? v.e : CF_EZERO;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    const int u = __shfl_xor_sync(0xffffffffu, e, o);
+    e = u > e ? u : e;
+  }
+  const int E = cf_sum_exponent(e, 16);
+  fx<K + 1> re, im;
+  fx_zero<K + 1>(re);
+  fx_zero<K + 1>(im);
+  if (has) cf_accumulate<K>(re, im, v, E);
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) {
+    fx<K + 1> a, b;
+#pragma unroll
+    for (int w = 0; w <= K; w++) {
+      a.w[w] = __shfl_xor_sync(0xffffffffu, re.w[w], o);
+      b.w[w] = __shfl_xor_sync(0xffffffffu, im.w[w], o);
+    }
+    re = ix_add<K + 1>(re, a);
+    im = ix_add<K + 1>(im, b);
+  }
+  if (E == CF_EZERO) return cf_zero<K>();
+  // the accumulator counts units of 2^(E - 64)
+  return cf_from_fixed<K, K + 1>(re, im, E - 64);
+}
+
+// X_k = D_k^-1 for the diagonal blocks of R[0:n, 0:n], one CTA of 256
+// threads per block.  The block's entries r_ij (i <= j) and 1/r_ii are first
+// converted to cf<K> in shared memory; then the 16-lane group c forms column
+// c of the inverse, one row per step from the diagonal up:
+//   X_cc = 1 / r_cc,  X_ic = -(1 / r_ii) sum_{j=i+1..c} r_ij X_jc  (i < c),
+// lane j forming r_ij X_jc and the group adding the products exactly.
+// Xinv[(k BSB + i) BSB + c] holds X_ic as cf<K> (2K+1 words), 0 below the
+// diagonal.
+template <int L>
+__global__ void __launch_bounds__(BSB * BSB) k_bs_inv(const double *__restrict__ Rm, int64_t ldr,
+                                                      int32_t n, const double *__restrict__ Zs,
+                                                      const double *__restrict__ sexp,
+                                                      double *__restrict__ Xinv,
+                                                      const int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, CW = 2 * K + 1;
+  __shared__ cf<K> sD[BSB][BSB];  // r_ij of the block
+  __shared__ cf<K> sX[BSB][BSB];  // X_ic
+  __shared__ cf<K> sZ[BSB];       // 1 / r_ii
+  if (*status != GN_OK) return;
+  const int k = blockIdx.x;
+  const int b0 = k * BSB;
+  const int bs = n - b0 < BSB ? n - b0 : BSB;
+  const int t = threadIdx.x, a = t / BSB, b = t % BSB;
+  sX[a][b] = cf_zero<K>();
+  if (a <= b && b < bs) {
+    const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)(b0 + b) * ldr + b0 + a) * W);
+    sD[a][b] = cf_from_fixed<K, K>(e[0], e[1], (int)sexp[b0 + b]);
+  }
+  if (t < bs) {
+    const uint64_t *z = (const uint64_t *)(Zs + (size_t)(b0 + t) * (K + 1));
+    fx<K> zr, zi;
+#pragma unroll
+    for (int w = 0; w < K; w++) zr.w[w] = z[w];
+    fx_zero<K>(zi);
+    sZ[t] = cf_from_fixed<K, K>(zr, zi, (int)Zs[(size_t)(b0 + t) * (K + 1) + K]);
+  }
+  __syncthreads();
+  const int c = a, j = b;  // group c, lane j
+  if (c < bs && j == 0) sX[c][c] = sZ[c];
+  __syncwarp();
+  for (int i = BSB - 2; i >= 0; i--) {
+    const bool has = i < c && c < bs && j > i && j <= c;
+    cf<K> p = cf_zero<K>();
+    if (has) p = cf_mul<K>(sD[i][j], sX[j][c]);
+    const cf<K> sum = cf_group16_sum<K>(p, has);
+    if (i < c && c < bs && j == 0) sX[i][c] = cf_neg<K>(cf_mul<K>(sZ[i], sum));
+    __syncwarp();
+  }
+  __syncthreads();  // column c was written by group c's warp
+  cf_put<K>(Xinv + ((size_t)(k * BSB + a) * BSB + b) * CW, sX[a][b]);
+}
+
+// R x = y with y = R[0:n, n], one CTA of BSB_THREADS threads, y in shared
+// memory.  Thread t works on the pair (row r = t / 16 of the current group,
+// column c = t % 16 of the current block).
+template <int L>
+__global__ void __launch_bounds__(BSB_THREADS) k_backsub_blk(
+    const double *__restrict__ Rm, int64_t ldr, int32_t n, const double *__restrict__ sexp,
+    const double *__restrict__ Xinv, double *__restrict__ dx, int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, KY = K + 2, CW = 2 * K + 1;
+  constexpr int GR = BSB_THREADS / BSB;  // rows per pass
+  extern __shared__ __align__(16) unsigned char bsm[];
+  fx<KY> *sY = (fx<KY> *)bsm;         // [n][2]
+  fx<K> *sX = (fx<K> *)(sY + 2 * n);  // [n][2]
+  int *sT = (int *)(sX + 2 * n);      // [n]
+  int *sFail = sT + n;
+  if (*status != GN_OK) return;
+  const int tid = threadIdx.x;
+  const int r = tid / BSB, c = tid % BSB;
+  const int sig = (int)sexp[n];
+  for (int i = tid; i < n; i += BSB_THREADS) {
+    const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)n * ldr + i) * W);
+    sY[2 * i] = ix_widen<K, KY>(e[0]);
+    sY[2 * i + 1] = ix_widen<K, KY>(e[1]);
+  }
+  if (tid == 0) *sFail = 0;
+  __syncthreads();
+  const int nb = (n + BSB - 1) / BSB;
+  // rows [i0, i1) -= R[rows, block k] x_block, GR rows per pass
+  auto update = [&](int k, int i0, int i1) {
+    const int b0 = k * BSB, bs = n - b0 < BSB ? n - b0 : BSB;
+    for (int base = i0; base < i1; base += GR) {
+      const int i = base + r;
+      fx<KY> ur, ui;
+      fx_zero<KY>(ur);
+      fx_zero<KY>(ui);
+      if (i < i1 && c < bs) {
+        const int j = b0 + c;
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)j * ldr + i) * W);
+        const int d = (int)sexp[j] + sT[j] - sig;
+        fx<KY> zr, zi;
+        fx_zero<KY>(zr);
+        fx_zero<KY>(zi);
+        bs_update<K, KY>(zr, zi, e[0], e[1], sX[2 * j], sX[2 * j + 1], d, sFail);
+        ur = zr;  // = -R_ij x_j in units of y
+        ui = zi;
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        fx<KY> a, b;
+#pragma unroll
+        for (int w = 0; w < KY; w++) {
+          a.w[w] = __shfl_xor_sync(0xffffffffu, ur.w[w], o);
+          b.w[w] = __shfl_xor_sync(0xffffffffu, ui.w[w], o);
+        }
+        ur = ix_add<KY>(ur, a);
+        ui = ix_add<KY>(ui, b);
+      }
+      if (c == 0 && i < i1) {
+        sY[2 * i] = ix_add<KY>(sY[2 * i], ur);
+        sY[2 * i + 1] = ix_add<KY>(sY[2 * i + 1], ui);
+      }
+    }
+  };
+  for (int k = nb - 1; k >= 0; k--) {
+    const int b0 = k * BSB, bs = n - b0 < BSB ? n - b0 : BSB;
+    // x_k = X_k y_k: pair (row b0 + r, column b0 + c).  Whole warps (the
+    // first BSB rows of pairs) take part in the group sums, with has = false
+    // past the block's size.
+    if (r < BSB) {
+      const bool has = r < bs && c >= r && c < bs;
+      cf<K> p = cf_zero<K>();
+      if (has) {
+        const cf<K> xk = cf_get<K>(Xinv + ((size_t)(k * BSB + r) * BSB + c) * CW);
+        const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
+        p = cf_mul<K>(xk, yc);
+      }
+      const cf<K> s = cf_group16_sum<K>(p, has);
+      if (c == 0 && r < bs) {
+        sX[2 * (b0 + r)] = s.re;
+        sX[2 * (b0 + r) + 1] = s.im;
+        sT[b0 + r] = s.e;
+      }
+    }
+    __syncthreads();
+    if (k > 0) {
+      update(k, b0 - BSB, b0);  // the next block's rows first
+      update(k, 0, b0 - BSB);
+    }
+    __syncthreads();
+  }
+  if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+  for (int l = tid; l < n; l += BSB_THREADS) {
+    double cr[L], ci[L];
+    const bool z = sT[l] == CF_EZERO;
+    fx_to_cascade<K, L>(sX[2 * l], z ? 0 : -sT[l], cr);
+    fx_to_cascade<K, L>(sX[2 * l + 1], z ? 0 : -sT[l], ci);
+#pragma unroll
+    for (int q = 0; q < L; q++) {
+      dx[(int64_t)l * W + q] = cr[q];
+      dx[(int64_t)l * W + L + q] = ci[q];
+    }
+  }
+}
+
+template <int L>
+__host__ __device__ constexpr size_t bsb_smem_bytes(int n) {
+  return (sizeof(fx<L + 2>) * 2 + sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 16;
+}
+
+}  // namespace gn

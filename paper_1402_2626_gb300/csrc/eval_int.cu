@@ -244,34 +244,6 @@ __global__ void __launch_bounds__(128) k_monomials_long_cf(
   }
 }
 
-// Exact-alignment term sums (Section 2.3).  The common exponent E is the
-// largest exponent among the terms plus the bit length of their count, so
-// that the sum cannot overflow; each K-limb mantissa goes to the top K limbs
-// of a (K+1)-limb accumulator (64 guard bits) and shifts right by E - e.  The
-// accumulator then holds the sum in units of 2^(E - 64), and the only error
-// is the truncation of each term below that unit.
-template <int K>
-__device__ __forceinline__ void cf_accumulate(fx<K + 1> &re, fx<K + 1> &im, const cf<K> &z, int E) {
-  if (z.e == CF_EZERO) return;
-  const int s = E - z.e;
-  if (s >= 64 * K + 62) return;  // entirely below the accumulator's unit
-  fx<K + 1> a, b;
-  a.w[0] = 0;
-  b.w[0] = 0;
-#pragma unroll
-  for (int w = 0; w < K; w++) {
-    a.w[w + 1] = z.re.w[w];
-    b.w[w + 1] = z.im.w[w];
-  }
-  re = ix_add<K + 1>(re, ix_sar<K + 1>(a, s));
-  im = ix_add<K + 1>(im, ix_sar<K + 1>(b, s));
-}
-
-// exponent of the sums of c terms whose largest exponent is emax
-__device__ __forceinline__ int cf_sum_exponent(int emax, int c) {
-  return emax == CF_EZERO ? CF_EZERO : emax + (32 - __clz(c > 0 ? c : 1));
-}
-
 template <int L>
 __device__ __forceinline__ void cf_store_cascade(double *dst, const fx<L + 1> &re, const fx<L + 1> &im,
                                                  int E, bool neg) {

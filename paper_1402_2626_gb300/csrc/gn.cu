@@ -49,6 +49,7 @@ static void ws_free(Workspace &w) {
   cudaFree(w.flags);
   cudaFree(w.Rm);
   cudaFree(w.Zs);
+  cudaFree(w.Xinv);
   if (w.h_norms) cudaFreeHost(w.h_norms);
   if (w.h_status) cudaFreeHost(w.h_status);
   w = Workspace();
@@ -76,6 +77,7 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   if (!e) e = dalloc(&w.flags, (n + 1) * MGS_FLAGS_PER_COLUMN);
   if (!e) e = dalloc(&w.Rm, W * (n + 1) * (n + 1));
   if (!e) e = dalloc(&w.Zs, (n + 1) * (L + 1));
+  if (!e) e = dalloc(&w.Xinv, bs_inv_doubles(s->n, L));
   if (!e && cudaMallocHost((void **)&w.h_norms, sizeof(double) * 3 * GN_REPORT_MAX) != cudaSuccess)
     e = GN_ENOMEM;
   if (!e && cudaMallocHost((void **)&w.h_status, sizeof(int32_t) * 2) != cudaSuccess) e = GN_ENOMEM;
@@ -308,7 +310,8 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
   }
   ws->fact = 0;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
-  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, Rm, Zs, d_dx, ws->status, st, true);
+  e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, scratch, flags, Rm, Zs, own ? nullptr : ws->Xinv,
+                   d_dx, ws->status, st, true);
   if (!e && cudaMemcpyAsync(ws->h_status, ws->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost,
                             st) != cudaSuccess)
     e = GN_ECUDA;
@@ -335,7 +338,7 @@ gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
   ws->fact = 0;
   if (cudaMemsetAsync(ws->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
   e = launch_lstsq(s, prec, m, n, d_Ab, ldAb, d_R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
-                   ws->status, st, true);
+                   nullptr, ws->status, st, true);
   if (e) return e;
   if (cudaMemcpyAsync(d_status, ws->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) !=
       cudaSuccess)
@@ -354,7 +357,7 @@ static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cu
   const int32_t N = s->N, n = s->n;
   gn_status e = launch_eval_sel(s, L, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
   if (e) return e;
-  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, ws->dx,
+  e = launch_lstsq(s, L, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, ws->Xinv, ws->dx,
                    ws->status, st, false);
   if (e) return e;
   const double *fnorm = ws->rinv + (int64_t)(n + 1) * L + n;  // original norm of the b column

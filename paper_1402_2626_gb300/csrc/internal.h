@@ -25,6 +25,7 @@ struct Workspace {
   uint32_t *flags = nullptr;    // [(n+1) * 8] pivot publication flags of the MGS kernel
   double *Rm = nullptr;         // mantissas of R (layout of R)
   double *Zs = nullptr;         // [(n+1) (L+1)] mantissas and exponents of 1/r_jj
+  double *Xinv = nullptr;       // inverses of R's 16 x 16 diagonal blocks (blocked back substitution)
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
   // what Ab, R, Rm, Zs and rinv hold: 0 nothing reusable; 1 / 2 the
@@ -113,13 +114,20 @@ inline size_t stage_words(int L) { return 2 * (size_t)L + 1; }
 // lstsq.cu
 // want_q: convert Q back to L-limb cascades (gn_lstsq); the Newton step skips it.
 // d_dx NULL: factorisation only (no back substitution).
+// Xinv: scratch of the blocked back substitution (NULL: one level at a time).
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
-                       double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q);
+                       double *Xinv, double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q);
 // whether launch_lstsq takes the integer-mantissa path for an m x (n+1) [A b]
 bool lstsq_int_path(const gn_system *s, int L, int32_t m, int32_t n);
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
-                             const double *rinv, double *dx, int32_t *status, cudaStream_t st);
+                             const double *rinv, double *Xinv, double *dx, int32_t *status,
+                             cudaStream_t st);
+// doubles of the inverse diagonal blocks (16 x 16, one complex value with an
+// exponent each: 2L+1 words) for n unknowns
+inline size_t bs_inv_doubles(int32_t n, int L) {
+  return (size_t)((n + 15) / 16) * 256 * (2 * (size_t)L + 1);
+}
 constexpr int BACKSUB_INT_MAX_N = 1024;
 // R and 1/r_kk as cascades from the mantissas the MGS launch left
 gn_status launch_mgs_r_out(int L, double *R, const double *Rm, int64_t ldr, int32_t ncols,

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(MGS_THREADS) k_update(int32_t n, double *__res
 template <int L>
 static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64_t lda, double *R,
                             double *rinv, double *nrm0, uint32_t *flags, double *Rm, double *Zs,
-                            double *dx, int32_t *status, cudaStream_t st, bool want_q) {
+                            double *Xinv, double *dx, int32_t *status, cudaStream_t st, bool want_q) {
   const int32_t ncols = n + 1;
   const int64_t ldr = ncols;
   if (use_int && flags && Rm && Zs && mgs_flow_clusters(L) > 0 && mgs_flow_fits(L, m, ncols)) {
@@ -263,7 +263,7 @@ static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64
       if (e) return e;
     }
     if (!dx) return GN_OK;
-    if (int_bs) return launch_backsub_int(L, Rm, ldr, n, Zs, rinv, dx, status, st);
+    if (int_bs) return launch_backsub_int(L, Rm, ldr, n, Zs, rinv, Xinv, dx, status, st);
     k_backsub<L><<<1, MGS_THREADS, 0, st>>>(R, ldr, n, rinv, dx, status);
     return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
   }
@@ -285,13 +285,13 @@ bool lstsq_int_path(const gn_system *s, int L, int32_t m, int32_t n) {
 
 gn_status launch_lstsq(gn_system *s, int L, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                        double *d_R, double *rinv, uint32_t *flags, double *Rm, double *Zs,
-                       double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q) {
+                       double *Xinv, double *d_dx, int32_t *d_status, cudaStream_t st, bool want_q) {
   double *nrm0 = rinv + (int64_t)(n + 1) * L;
   const bool ui = lstsq_int(s);
   switch (L) {
-    case 1: return lstsq_impl<1>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, d_dx, d_status, st, want_q);
-    case 2: return lstsq_impl<2>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, d_dx, d_status, st, want_q);
-    case 4: return lstsq_impl<4>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, d_dx, d_status, st, want_q);
+    case 1: return lstsq_impl<1>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, Xinv, d_dx, d_status, st, want_q);
+    case 2: return lstsq_impl<2>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, Xinv, d_dx, d_status, st, want_q);
+    case 4: return lstsq_impl<4>(ui, m, n, d_Ab, ldAb, d_R, rinv, nrm0, flags, Rm, Zs, Xinv, d_dx, d_status, st, want_q);
   }
   return GN_EINVAL;
 }

@@ -31,6 +31,7 @@
 #include <mutex>
 
 #include "bs.cuh"
+#include "bsb.cuh"
 #include "ifx.cuh"
 #include "internal.h"
 #include "mw.cuh"
@@ -227,9 +228,36 @@ static gn_status bs_launch(const double *Rm, int64_t ldr, int32_t n, const doubl
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
+template <int L>
+static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                            const double *rinv, double *Xinv, double *dx, int32_t *status,
+                            cudaStream_t st) {
+  const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
+  const int nb = (n + BSB - 1) / BSB;
+  k_bs_inv<L><<<(unsigned)nb, BSB * BSB, 0, st>>>(Rm, ldr, n, Zs, sexp, Xinv, status);
+  const size_t bytes = bsb_smem_bytes<L>(n);
+  if (bytes > 48 * 1024 &&
+      cudaFuncSetAttribute(k_backsub_blk<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess)
+    return GN_ECUDA;
+  k_backsub_blk<L><<<1, BSB_THREADS, bytes, st>>>(Rm, ldr, n, sexp, Xinv, dx, status);
+  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
-                             const double *rinv, double *dx, int32_t *status, cudaStream_t st) {
+                             const double *rinv, double *Xinv, double *dx, int32_t *status,
+                             cudaStream_t st) {
   if (n < 1 || n > 2 * BS_MAX_THREADS) return GN_EINVAL;
+  // blocked with inverse diagonal blocks from two blocks up (one level at a
+  // time below that, or without the scratch)
+  if (Xinv && n >= 2 * BSB) {
+    switch (L) {
+      case 1: return bsb_launch<1>(Rm, ldr, n, Zs, rinv, Xinv, dx, status, st);
+      case 2: return bsb_launch<2>(Rm, ldr, n, Zs, rinv, Xinv, dx, status, st);
+      case 4: return bsb_launch<4>(Rm, ldr, n, Zs, rinv, Xinv, dx, status, st);
+    }
+    return GN_EINVAL;
+  }
   switch (L) {
     case 1: return bs_launch<1>(Rm, ldr, n, Zs, rinv, dx, status, st);
     case 2: return bs_launch<2>(Rm, ldr, n, Zs, rinv, dx, status, st);
