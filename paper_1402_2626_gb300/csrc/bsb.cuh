@@ -17,11 +17,15 @@
 // Entries of X_k are complex values with one binary exponent (cf.cuh).
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include "bs.cuh"
 #include "cf.cuh"
 #include "internal.h"
 
 namespace gn {
+
+namespace cg = cooperative_groups;
 
 constexpr int BSB = 16;              // block size
 constexpr int BSB_THREADS = 512;     // threads of the solve (32 rows x 16 columns per pass)
@@ -268,9 +272,140 @@ __global__ void __launch_bounds__(BSB_THREADS) k_backsub_blk(
   }
 }
 
+// The same solve on a cluster of BSC CTAs: block b of rows (and of y) lives
+// in CTA b mod BSC.  Per block k, from the last: the owner of block k-1
+// subtracts R_(k-1),k x_k from its rows and forms x_(k-1) = X_(k-1) y_(k-1)
+// at once, storing it into every CTA's shared memory (double-buffered by the
+// parity of the block); every CTA then subtracts R_ik x_k from its other
+// rows; one cluster barrier ends the step.  The chain per block is one
+// update pass, one inverse pass and a barrier; the bulk of the n^2/2
+// products is split over the cluster's SMs.  Every CTA runs every barrier
+// (no early exit after the first one).
+constexpr int BSC = 8;
+
+template <int L>
+__global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
+    const double *__restrict__ Rm, int64_t ldr, int32_t n, const double *__restrict__ sexp,
+    const double *__restrict__ Xinv, double *__restrict__ dx, int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, KY = K + 2, CW = 2 * K + 1;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  fx<KY> *sY = (fx<KY> *)bsm;              // [n][2], the rows of this CTA's blocks
+  fx<K> *sXc = (fx<K> *)(sY + 2 * n);      // [2][BSB][2] x of the current / next block
+  int *sTc = (int *)(sXc + 2 * BSB * 2);   // [2][BSB]
+  int *sFail = sTc + 2 * BSB;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const bool run = *status == GN_OK;  // the same for every CTA: nothing writes it before the end
+  const int tid = threadIdx.x;
+  const int r = tid / BSB, c = tid % BSB;
+  const int sig = (int)sexp[n];
+  const int nb = (n + BSB - 1) / BSB;
+  auto bsz = [&](int b) { return n - b * BSB < BSB ? n - b * BSB : BSB; };
+  if (run)
+    for (int b = rank; b < nb; b += BSC)
+      for (int q = tid; q < bsz(b); q += BSB_THREADS) {
+        const int i = b * BSB + q;
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)n * ldr + i) * W);
+        sY[2 * i] = ix_widen<K, KY>(e[0]);
+        sY[2 * i + 1] = ix_widen<K, KY>(e[1]);
+      }
+  if (tid == 0) *sFail = 0;
+  // x_k = X_k y_k for a block this CTA owns, into buffer buf of every CTA
+  // and into dx
+  auto xstep = [&](int k, int buf) {
+    const int b0 = k * BSB, bs = bsz(k);
+    if (r < BSB) {  // whole warps: the first BSB rows of pairs
+      const bool has = r < bs && c >= r && c < bs;
+      cf<K> p = cf_zero<K>();
+      if (has) {
+        const cf<K> xk = cf_get<K>(Xinv + ((size_t)(k * BSB + r) * BSB + c) * CW);
+        const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
+        p = cf_mul<K>(xk, yc);
+      }
+      const cf<K> sx = cf_group16_sum<K>(p, has);
+      if (c == 0 && r < bs) {
+        for (int q = 0; q < BSC; q++) {
+          fx<K> *rx = cl.map_shared_rank(sXc, q) + 2 * (buf * BSB + r);
+          rx[0] = sx.re;
+          rx[1] = sx.im;
+          cl.map_shared_rank(sTc, q)[buf * BSB + r] = sx.e;
+        }
+        double cr[L], ci[L];
+        const bool z = sx.e == CF_EZERO;
+        fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
+        fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          dx[(int64_t)(b0 + r) * W + q] = cr[q];
+          dx[(int64_t)(b0 + r) * W + L + q] = ci[q];
+        }
+      }
+    }
+  };
+  // rows of the owned blocks b with lo <= b < hi (b = rank mod BSC) minus
+  // R[rows, block k] x_k (x_k in buffer buf); two blocks of rows per pass
+  auto update = [&](int k, int buf, int lo, int hi) {
+    const int j0 = k * BSB, jb = bsz(k);
+    int first = lo + ((rank - lo) % BSC + BSC) % BSC;  // first owned block >= lo
+    for (int b2 = first; b2 < hi; b2 += 2 * BSC) {
+      const int b = b2 + (r / BSB) * BSC;  // this pair's block
+      const int i = b * BSB + (r % BSB);
+      const bool act = b < hi && (r % BSB) < bsz(b < nb ? b : 0) && c < jb;
+      fx<KY> ur, ui;
+      fx_zero<KY>(ur);
+      fx_zero<KY>(ui);
+      if (act) {
+        const int j = j0 + c;
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)j * ldr + i) * W);
+        const int d = (int)sexp[j] + sTc[buf * BSB + c] - sig;
+        bs_update<K, KY>(ur, ui, e[0], e[1], sXc[2 * (buf * BSB + c)], sXc[2 * (buf * BSB + c) + 1], d,
+                         sFail);
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        fx<KY> a, bb;
+#pragma unroll
+        for (int w = 0; w < KY; w++) {
+          a.w[w] = __shfl_xor_sync(0xffffffffu, ur.w[w], o);
+          bb.w[w] = __shfl_xor_sync(0xffffffffu, ui.w[w], o);
+        }
+        ur = ix_add<KY>(ur, a);
+        ui = ix_add<KY>(ui, bb);
+      }
+      if (c == 0 && b < hi && (r % BSB) < bsz(b < nb ? b : 0)) {
+        sY[2 * i] = ix_add<KY>(sY[2 * i], ur);
+        sY[2 * i + 1] = ix_add<KY>(sY[2 * i + 1], ui);
+      }
+    }
+  };
+  __syncthreads();
+  cl.sync();  // rows loaded; every CTA started (DSMEM stores may target it)
+  if (run && rank == (nb - 1) % BSC) xstep(nb - 1, (nb - 1) & 1);
+  cl.sync();
+  for (int k = nb - 1; k >= 1; k--) {
+    const int buf = k & 1;
+    if (run) {
+      if (rank == (k - 1) % BSC) {
+        update(k, buf, k - 1, k);  // block k-1 first
+        __syncthreads();
+        xstep(k - 1, buf ^ 1);
+      }
+      update(k, buf, 0, k - 1);  // the other owned blocks above
+    }
+    cl.sync();
+  }
+  if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+}
+
 template <int L>
 __host__ __device__ constexpr size_t bsb_smem_bytes(int n) {
   return (sizeof(fx<L + 2>) * 2 + sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 16;
+}
+
+template <int L>
+__host__ __device__ constexpr size_t bsc_smem_bytes(int n) {
+  return sizeof(fx<L + 2>) * 2 * (size_t)(n > 0 ? n : 1) + sizeof(fx<L>) * 2 * 2 * BSB +
+         sizeof(int) * (2 * BSB + 4);
 }
 
 }  // namespace gn

@@ -89,6 +89,7 @@ gn_status workspace_get(gn_system *s, int L, Workspace **out) {
   }
   // query cluster occupancy now: never during a stream capture
   mgs_flow_clusters(L);
+  backsub_prepare(L);
   w.ready = true;
   return GN_OK;
 }

@@ -123,6 +123,9 @@ bool lstsq_int_path(const gn_system *s, int L, int32_t m, int32_t n);
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                              const double *rinv, double *Xinv, double *dx, int32_t *status,
                              cudaStream_t st);
+// query (once) whether the cluster back substitution can be placed; never
+// call during a stream capture
+void backsub_prepare(int L);
 // doubles of the inverse diagonal blocks (16 x 16, one complex value with an
 // exponent each: 2L+1 words) for n unknowns
 inline size_t bs_inv_doubles(int32_t n, int L) {

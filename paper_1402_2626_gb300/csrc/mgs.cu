@@ -228,6 +228,38 @@ static gn_status bs_launch(const double *Rm, int64_t ldr, int32_t n, const doubl
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
+// whether a cluster of BSC solve CTAs can be placed (queried once per precision)
+template <int L>
+static bool bsc_available() {
+  static int ok = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  if (ok < 0) {
+    const size_t bytes = bsc_smem_bytes<L>(2 * BS_MAX_THREADS);
+    ok = 0;
+    if (cudaFuncSetAttribute(k_backsub_cl<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_backsub_cl<L>, cudaFuncAttributeNonPortableClusterSizeAllowed, 0) ==
+            cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(BSC);
+      cfg.blockDim = dim3(BSB_THREADS);
+      cfg.dynamicSmemBytes = bytes;
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = BSC;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_backsub_cl<L>, &cfg) == cudaSuccess && nc > 0) ok = 1;
+    }
+    cudaGetLastError();
+  }
+  return ok == 1;
+}
+
 template <int L>
 static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const double *Zs,
                             const double *rinv, double *Xinv, double *dx, int32_t *status,
@@ -235,6 +267,24 @@ static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const doub
   const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
   const int nb = (n + BSB - 1) / BSB;
   k_bs_inv<L><<<(unsigned)nb, BSB * BSB, 0, st>>>(Rm, ldr, n, Zs, sexp, Xinv, status);
+  if (bsc_available<L>()) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(BSC);
+    cfg.blockDim = dim3(BSB_THREADS);
+    cfg.dynamicSmemBytes = bsc_smem_bytes<L>(n);
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = BSC;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_backsub_cl<L>, (const double *)Rm, ldr, n, sexp,
+                           (const double *)Xinv, dx, status) != cudaSuccess)
+      return GN_ECUDA;
+    return GN_OK;
+  }
   const size_t bytes = bsb_smem_bytes<L>(n);
   if (bytes > 48 * 1024 &&
       cudaFuncSetAttribute(k_backsub_blk<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
@@ -242,6 +292,14 @@ static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const doub
     return GN_ECUDA;
   k_backsub_blk<L><<<1, BSB_THREADS, bytes, st>>>(Rm, ldr, n, sexp, Xinv, dx, status);
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+}
+
+void backsub_prepare(int L) {
+  switch (L) {
+    case 1: bsc_available<1>(); break;
+    case 2: bsc_available<2>(); break;
+    case 4: bsc_available<4>(); break;
+  }
 }
 
 gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
