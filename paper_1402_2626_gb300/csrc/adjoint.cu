@@ -11,7 +11,10 @@
 //   lambda = (J^+)^H g = Q w,  R^H w = g.
 // Three launches after the factorisation (evaluation and MGS are the Newton
 // step's own kernels, on [J, -f] at x):
-//   k_adj_fwdsub  R^H w = g by forward substitution (one CTA),
+//   R^H w = g by forward substitution: blocked on R's integer mantissas
+//                 (k_fwdsub_cl, with the inverse diagonal blocks) when the
+//                 factorisation came from the integer MGS, else k_adj_fwdsub
+//                 (one CTA, cascade arithmetic),
 //   k_adj_lambda  lambda = Q w (one CTA per row),
 //   k_adj_grad    grad_t = -lambda_i conj(x^{a_t}) (one thread per term).
 // The arithmetic is the cascade arithmetic of mw.cuh at precision L.
@@ -143,9 +146,16 @@ __global__ void k_set_coef(int64_t T, const double *__restrict__ src, int32_t cl
 
 template <int L>
 static gn_status adjoint_tail(gn_system *s, Workspace *ws, const double *d_x, const double *d_g,
-                              double *d_grad, double *lam, cudaStream_t st) {
+                              double *d_grad, double *lam, bool int_fact, cudaStream_t st) {
   const int32_t N = s->N, n = s->n;
-  k_adj_fwdsub<L><<<1, ADJ_THREADS, 0, st>>>(ws->R, n + 1, n, ws->rinv, d_g, ws->dx, ws->status);
+  if (int_fact && fwdsub_int_available(L, n)) {
+    // blocked on the integer mantissas of R (the diagonal blocks' inverses)
+    gn_status e = launch_fwdsub_int(L, ws->Rm, n + 1, n, ws->Zs, ws->rinv, ws->Xinv, d_g, ws->dx,
+                                    ws->status, st);
+    if (e) return e;
+  } else {
+    k_adj_fwdsub<L><<<1, ADJ_THREADS, 0, st>>>(ws->R, n + 1, n, ws->rinv, d_g, ws->dx, ws->status);
+  }
   k_adj_lambda<L><<<(unsigned)N, ADJ_THREADS, 0, st>>>(ws->Ab, N, N, n, ws->dx, lam, ws->status);
   if (s->T > 0)
     k_adj_grad<L><<<(unsigned)((s->T + 127) / 128), 128, 0, st>>>(
@@ -181,6 +191,7 @@ extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, c
   } else {
     // [J, -f] at x and its factorisation, Q and R as cascades
     ws->fact = 0;
+    ws->fact_int = lstsq_int_path(s, prec, N, n) ? 1 : 0;
     e = launch_eval_sel(s, prec, d_x, ws->Ab + (int64_t)n * N * W, 1, ws->Ab, N, st);
     if (!e)
       e = launch_lstsq(s, prec, N, n, ws->Ab, N, ws->R, ws->rinv, ws->flags, ws->Rm, ws->Zs, nullptr,
@@ -188,9 +199,9 @@ extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, c
   }
   if (!e) {
     switch (prec) {
-      case 1: e = adjoint_tail<1>(s, ws, d_x, d_g, d_grad, lam, st); break;
-      case 2: e = adjoint_tail<2>(s, ws, d_x, d_g, d_grad, lam, st); break;
-      case 4: e = adjoint_tail<4>(s, ws, d_x, d_g, d_grad, lam, st); break;
+      case 1: e = adjoint_tail<1>(s, ws, d_x, d_g, d_grad, lam, ws->fact_int != 0, st); break;
+      case 2: e = adjoint_tail<2>(s, ws, d_x, d_g, d_grad, lam, ws->fact_int != 0, st); break;
+      case 4: e = adjoint_tail<4>(s, ws, d_x, d_g, d_grad, lam, ws->fact_int != 0, st); break;
     }
   }
   if (e) return e;

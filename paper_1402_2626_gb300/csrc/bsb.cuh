@@ -397,6 +397,153 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
   if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
 }
 
+// R^H w = g (the adjoint's forward substitution) on the same cluster and the
+// same inverse blocks: the diagonal blocks of R^H are D_k^H, with inverses
+// X_k^H.  Blocks run forward; the owner of block k+1 subtracts
+// (R^H)_(k+1),k w_k = conj(R_k,(k+1))^T w_k from its rows and forms
+// w_(k+1) = X_(k+1)^H g_(k+1) at once.  g (L-limb cascades) is taken to
+// fixed point at one scale 2^sig, max |g| < 2^(64K-3+sig), two limbs of
+// headroom above it; the products conj(r_ji) w_j carry column i's exponent.
+template <int L>
+__global__ void __launch_bounds__(BSB_THREADS, 1) k_fwdsub_cl(
+    const double *__restrict__ Rm, int64_t ldr, int32_t n, const double *__restrict__ sexp,
+    const double *__restrict__ Xinv, const double *__restrict__ g, double *__restrict__ w,
+    int32_t *__restrict__ status) {
+  constexpr int K = L, W = 2 * L, KY = K + 2, CW = 2 * K + 1;
+  extern __shared__ __align__(16) unsigned char bsm[];
+  fx<KY> *sY = (fx<KY> *)bsm;              // [n][2], the rows of this CTA's blocks
+  fx<K> *sXc = (fx<K> *)(sY + 2 * n);      // [2][BSB][2] w of the current / next block
+  int *sTc = (int *)(sXc + 2 * BSB * 2);   // [2][BSB]
+  int *sFail = sTc + 2 * BSB;
+  int *sE = sFail + 1;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const bool run = *status == GN_OK;
+  const int tid = threadIdx.x;
+  const int r = tid / BSB, c = tid % BSB;
+  const int nb = (n + BSB - 1) / BSB;
+  auto bsz = [&](int b) { return n - b * BSB < BSB ? n - b * BSB : BSB; };
+  // the scale: the largest exponent of a leading limb (the same in every CTA)
+  if (tid == 0) *sE = -100000;
+  __syncthreads();
+  {
+    int em = -100000;
+    for (int i = tid; i < n; i += BSB_THREADS) {
+      const double a = fmax(fabs(g[(int64_t)i * W]), fabs(g[(int64_t)i * W + L]));
+      if (a > 0.0) em = max(em, fx_exponent_of(a));
+    }
+    atomicMax(sE, em);
+  }
+  if (tid == 0) *sFail = 0;
+  __syncthreads();
+  // |g| < 2^(E+1) (one bit for the lower limbs); mantissas at 2^(64K-4-E)
+  const int sig = (*sE == -100000) ? 0 : *sE + 4 - 64 * K;
+  if (run)
+    for (int b = rank; b < nb; b += BSC)
+      for (int q = tid; q < bsz(b); q += BSB_THREADS) {
+        const int i = b * BSB + q;
+        fx<K> re, im;
+        fx_zero<K>(re);
+        fx_zero<K>(im);
+#pragma unroll
+        for (int l = 0; l < L; l++) {
+          fx_add_double<K>(re, g[(int64_t)i * W + l], -sig);
+          fx_add_double<K>(im, g[(int64_t)i * W + L + l], -sig);
+        }
+        sY[2 * i] = ix_widen<K, KY>(re);
+        sY[2 * i + 1] = ix_widen<K, KY>(im);
+      }
+  auto xstep = [&](int k, int buf) {
+    const int b0 = k * BSB, bs = bsz(k);
+    if (r < BSB) {
+      const bool has = r < bs && c <= r;
+      cf<K> p = cf_zero<K>();
+      if (has) {
+        // (X_k^H)_rc = conj(X_k cr)
+        cf<K> xk = cf_get<K>(Xinv + ((size_t)(k * BSB + c) * BSB + r) * CW);
+        fx<K> z;
+        fx_zero<K>(z);
+        xk.im = ix_sub<K>(z, xk.im);
+        const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
+        p = cf_mul<K>(xk, yc);
+      }
+      const cf<K> sx = cf_group16_sum<K>(p, has);
+      if (c == 0 && r < bs) {
+        for (int q = 0; q < BSC; q++) {
+          fx<K> *rx = cl.map_shared_rank(sXc, q) + 2 * (buf * BSB + r);
+          rx[0] = sx.re;
+          rx[1] = sx.im;
+          cl.map_shared_rank(sTc, q)[buf * BSB + r] = sx.e;
+        }
+        double cr[L], ci[L];
+        const bool z = sx.e == CF_EZERO;
+        fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
+        fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
+#pragma unroll
+        for (int q = 0; q < L; q++) {
+          w[(int64_t)(b0 + r) * W + q] = cr[q];
+          w[(int64_t)(b0 + r) * W + L + q] = ci[q];
+        }
+      }
+    }
+  };
+  // rows of the owned blocks b with lo <= b < hi minus conj(R[block k, rows])^T w_k
+  auto update = [&](int k, int buf, int lo, int hi) {
+    const int j0 = k * BSB, jb = bsz(k);
+    int first = lo + ((rank - lo) % BSC + BSC) % BSC;
+    for (int b2 = first; b2 < hi; b2 += 2 * BSC) {
+      const int b = b2 + (r / BSB) * BSC;
+      const int i = b * BSB + (r % BSB);
+      const bool rowok = b < hi && (r % BSB) < bsz(b < nb ? b : 0);
+      const bool act = rowok && c < jb;
+      fx<KY> ur, ui;
+      fx_zero<KY>(ur);
+      fx_zero<KY>(ui);
+      if (act) {
+        const int j = j0 + c;
+        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)i * ldr + j) * W);  // r_ji, column i
+        fx<K> z;
+        fx_zero<K>(z);
+        const int d = (int)sexp[i] + sTc[buf * BSB + c] - sig;
+        bs_update<K, KY>(ur, ui, e[0], ix_sub<K>(z, e[1]), sXc[2 * (buf * BSB + c)],
+                         sXc[2 * (buf * BSB + c) + 1], d, sFail);
+      }
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {
+        fx<KY> a, bb;
+#pragma unroll
+        for (int q = 0; q < KY; q++) {
+          a.w[q] = __shfl_xor_sync(0xffffffffu, ur.w[q], o);
+          bb.w[q] = __shfl_xor_sync(0xffffffffu, ui.w[q], o);
+        }
+        ur = ix_add<KY>(ur, a);
+        ui = ix_add<KY>(ui, bb);
+      }
+      if (c == 0 && rowok) {
+        sY[2 * i] = ix_add<KY>(sY[2 * i], ur);
+        sY[2 * i + 1] = ix_add<KY>(sY[2 * i + 1], ui);
+      }
+    }
+  };
+  __syncthreads();
+  cl.sync();
+  if (run && rank == 0 % BSC) xstep(0, 0);
+  cl.sync();
+  for (int k = 0; k < nb - 1; k++) {
+    const int buf = k & 1;
+    if (run) {
+      if (rank == (k + 1) % BSC) {
+        update(k, buf, k + 1, k + 2);  // block k+1 first
+        __syncthreads();
+        xstep(k + 1, buf ^ 1);
+      }
+      update(k, buf, k + 2, nb);  // the other owned blocks below
+    }
+    cl.sync();
+  }
+  if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+}
+
 template <int L>
 __host__ __device__ constexpr size_t bsb_smem_bytes(int n) {
   return (sizeof(fx<L + 2>) * 2 + sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 16;

@@ -438,7 +438,10 @@ extern "C" gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t 
   run = (gn_status)ws->h_status[0];
   done = ws->h_status[1];
   // the workspace now holds the factorisation of the last step's J
-  if (run == GN_OK && done >= 1) ws->fact = lstsq_int_path(s, prec, s->N, s->n) ? 1 : 2;
+  if (run == GN_OK && done >= 1) {
+    ws->fact_int = lstsq_int_path(s, prec, s->N, s->n) ? 1 : 0;
+    ws->fact = ws->fact_int ? 1 : 2;
+  }
   if (run == GN_OK && tol > 0.0 && !converged) run = GN_ENOCONV;
   if (report) {
     memset(report, 0, sizeof(*report));

@@ -31,6 +31,7 @@ struct Workspace {
   // what Ab, R, Rm, Zs and rinv hold: 0 nothing reusable; 1 / 2 the
   // factorisation of the last gn_newton step, integer mantissas / cascades
   int fact = 0;
+  int fact_int = 0;  // that factorisation came from the integer MGS (Rm, Zs valid)
   // CUDA graph of one Newton step for a given x pointer and stream
   cudaGraphExec_t step_exec = nullptr;
   const double *graph_x = nullptr;
@@ -126,6 +127,12 @@ gn_status launch_backsub_int(int L, const double *Rm, int64_t ldr, int32_t n, co
 // query (once) whether the cluster back substitution can be placed; never
 // call during a stream capture
 void backsub_prepare(int L);
+// R^H w = g (cascades in and out) on the integer mantissas of R, blocked on
+// a cluster (the adjoint's forward substitution); available for 32 <= n <= 1024
+bool fwdsub_int_available(int L, int32_t n);
+gn_status launch_fwdsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                            const double *rinv, double *Xinv, const double *g, double *w,
+                            int32_t *status, cudaStream_t st);
 // doubles of the inverse diagonal blocks (16 x 16, one complex value with an
 // exponent each: 2L+1 words) for n unknowns
 inline size_t bs_inv_doubles(int32_t n, int L) {

@@ -294,11 +294,88 @@ static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const doub
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
+// the same for the forward substitution of the adjoint
+template <int L>
+static bool fsc_available() {
+  static int ok = -1;
+  static std::mutex mu;
+  std::lock_guard<std::mutex> g(mu);
+  if (ok < 0) {
+    const size_t bytes = bsc_smem_bytes<L>(2 * BS_MAX_THREADS);
+    ok = 0;
+    if (cudaFuncSetAttribute(k_fwdsub_cl<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) ==
+        cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(BSC);
+      cfg.blockDim = dim3(BSB_THREADS);
+      cfg.dynamicSmemBytes = bytes;
+      cudaLaunchAttribute attr;
+      attr.id = cudaLaunchAttributeClusterDimension;
+      attr.val.clusterDim.x = BSC;
+      attr.val.clusterDim.y = 1;
+      attr.val.clusterDim.z = 1;
+      cfg.attrs = &attr;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_fwdsub_cl<L>, &cfg) == cudaSuccess && nc > 0) ok = 1;
+    }
+    cudaGetLastError();
+  }
+  return ok == 1;
+}
+
+template <int L>
+static gn_status fsc_launch(const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                            const double *rinv, double *Xinv, const double *g, double *w,
+                            int32_t *status, cudaStream_t st) {
+  if (!fsc_available<L>()) return GN_EINVAL;
+  const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
+  const int nb = (n + BSB - 1) / BSB;
+  k_bs_inv<L><<<(unsigned)nb, BSB * BSB, 0, st>>>(Rm, ldr, n, Zs, sexp, Xinv, status);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(BSC);
+  cfg.blockDim = dim3(BSB_THREADS);
+  cfg.dynamicSmemBytes = bsc_smem_bytes<L>(n);
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = BSC;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  if (cudaLaunchKernelEx(&cfg, k_fwdsub_cl<L>, (const double *)Rm, ldr, n, sexp, (const double *)Xinv, g,
+                         w, status) != cudaSuccess)
+    return GN_ECUDA;
+  return GN_OK;
+}
+
+bool fwdsub_int_available(int L, int32_t n) {
+  if (n < 2 * BSB || n > 2 * BS_MAX_THREADS) return false;
+  switch (L) {
+    case 1: return fsc_available<1>();
+    case 2: return fsc_available<2>();
+    case 4: return fsc_available<4>();
+  }
+  return false;
+}
+
+gn_status launch_fwdsub_int(int L, const double *Rm, int64_t ldr, int32_t n, const double *Zs,
+                            const double *rinv, double *Xinv, const double *g, double *w,
+                            int32_t *status, cudaStream_t st) {
+  switch (L) {
+    case 1: return fsc_launch<1>(Rm, ldr, n, Zs, rinv, Xinv, g, w, status, st);
+    case 2: return fsc_launch<2>(Rm, ldr, n, Zs, rinv, Xinv, g, w, status, st);
+    case 4: return fsc_launch<4>(Rm, ldr, n, Zs, rinv, Xinv, g, w, status, st);
+  }
+  return GN_EINVAL;
+}
+
 void backsub_prepare(int L) {
   switch (L) {
-    case 1: bsc_available<1>(); break;
-    case 2: bsc_available<2>(); break;
-    case 4: bsc_available<4>(); break;
+    case 1: bsc_available<1>(); fsc_available<1>(); break;
+    case 2: bsc_available<2>(); fsc_available<2>(); break;
+    case 4: bsc_available<4>(); fsc_available<4>(); break;
   }
 }
 

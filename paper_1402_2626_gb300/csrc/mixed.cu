@@ -9,7 +9,9 @@
 //      step one replay of the double-precision step graph;
 //   2. refinement at precision L with the last double factorisation frozen:
 //      b = -f(x) evaluated at precision L (Section 2), y = Q^H b in double,
-//      R dx = y by back substitution in double, x <- x + dx at precision L.
+//      R dx = y by back substitution (the blocked solve on the integer
+//      mantissas the double MGS left, or in double after an FP64 one),
+//      x <- x + dx at precision L.
 // Phase 2 converges linearly, by about kappa(J) times the unit roundoff of
 // double per step, to the precision of the residuals; for a consistent
 // system this is the root at precision L.  The factorisation, the cost the
@@ -88,8 +90,42 @@ __global__ void __launch_bounds__(MIX_THREADS) k_mix_qhb(const double *__restric
   }
 }
 
+// y (double complex, column n of the cascade R) into column n of the
+// mantissas Rm as one-limb fixed point at a common scale 2^sig, |y| / 2^sig
+// < 2^61 (the format MGS leaves its last column in), sig into sexp[n]; one
+// CTA.
+__global__ void __launch_bounds__(MIX_THREADS) k_mix_y_fixed(const double *__restrict__ R,
+                                                            double *__restrict__ Rm, int64_t ldr,
+                                                            int32_t n, double *__restrict__ sexp,
+                                                            const int32_t *__restrict__ status) {
+  __shared__ double smax[MIX_THREADS];
+  if (*status != GN_OK) return;
+  double m = 0.0;
+  for (int i = threadIdx.x; i < n; i += MIX_THREADS) {
+    const double *y = R + ((int64_t)n * ldr + i) * 2;
+    m = fmax(m, fmax(fabs(y[0]), fabs(y[1])));
+  }
+  smax[threadIdx.x] = m;
+  __syncthreads();
+  for (int h = MIX_THREADS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + h]);
+    __syncthreads();
+  }
+  int e = 0;
+  if (smax[0] > 0.0) frexp(smax[0], &e);  // max |y| < 2^e
+  const int sig = e - 61;
+  for (int i = threadIdx.x; i < n; i += MIX_THREADS) {
+    const double *y = R + ((int64_t)n * ldr + i) * 2;
+    long long *d = (long long *)(Rm + ((int64_t)n * ldr + i) * 2);
+    d[0] = llrint(ldexp(y[0], -sig));
+    d[1] = llrint(ldexp(y[1], -sig));
+  }
+  if (threadIdx.x == 0) sexp[n] = (double)sig;
+}
+
 template <int L>
-static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double *d_x, cudaStream_t st) {
+static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double *d_x, bool int_fact,
+                             cudaStream_t st) {
   const int32_t N = s->N, n = s->n;
   const int64_t W = 2 * L;
   double *negf = wL->Ab + (int64_t)n * N * W;
@@ -98,7 +134,15 @@ static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double 
   if (e) return e;
   k_mix_qhb<L><<<(unsigned)n, MIX_THREADS, 0, st>>>(w1->Ab, N, N, n, negf, w1->R, n + 1, fnorm,
                                                     wL->status);
-  e = launch_backsub_fp64(1, w1->R, n + 1, n, w1->rinv, w1->dx, wL->status, st);
+  if (int_fact && n <= BACKSUB_INT_MAX_N) {
+    // the integer factors of the last double step are still in place: the
+    // blocked back substitution on them
+    double *sexp = w1->rinv + 2 * (size_t)(n + 1);
+    k_mix_y_fixed<<<1, MIX_THREADS, 0, st>>>(w1->R, w1->Rm, n + 1, n, sexp, wL->status);
+    e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, wL->status, st);
+  } else {
+    e = launch_backsub_fp64(1, w1->R, n + 1, n, w1->rinv, w1->dx, wL->status, st);
+  }
   if (e) return e;
   k_mix_spread<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, w1->dx, wL->dx);
   return launch_update(L, n, d_x, wL->dx, fnorm, wL->norms, wL->status, st);
@@ -141,6 +185,7 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
   }
   if (e) return e;
   // the last step's factors as doubles
+  const bool int_fact = w1->fact == 1;
   if (w1->fact == 1) {
     e = launch_mgs_to_cascade(1, w1->Ab, s->N, s->N, n + 1, w1->rinv, w1->status, st);
     if (!e) e = launch_mgs_r_out(1, w1->R, w1->Rm, n + 1, n + 1, w1->rinv, w1->status, st);
@@ -159,7 +204,7 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
     return GN_ECUDA;
   bool converged = false;
   for (int32_t k = 0; k < refine_steps; k++) {
-    e = L == 2 ? refine_step<2>(s, w1, wL, d_x, st) : refine_step<4>(s, w1, wL, d_x, st);
+    e = L == 2 ? refine_step<2>(s, w1, wL, d_x, int_fact, st) : refine_step<4>(s, w1, wL, d_x, int_fact, st);
     if (e) return e;
     if (tol > 0.0) {
       if (cudaMemcpyAsync(wL->h_status, wL->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=

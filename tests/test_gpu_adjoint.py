@@ -52,6 +52,8 @@ def _check(got, want, L, what):
 SMALL = [
     ("square", dict(N=24, n=24, M=(12, 30), k=(1, 6), dmax=3, seed=501)),
     ("overdetermined ragged", dict(N=45, n=30, M=(10, 20), k=(1, 5), dmax=3, seed=502)),
+    # three 16-column blocks, the last partial: the blocked forward substitution
+    ("blocked ragged", dict(N=50, n=40, M=(10, 20), k=(1, 5), dmax=3, seed=507)),
 ]
 
 
