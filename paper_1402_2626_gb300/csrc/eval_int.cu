@@ -43,6 +43,13 @@ __device__ __forceinline__ cf<K> cf_ld(const double *p) {
   return z;
 }
 
+// the exponent factor d of Section 2.3 (d = 1: the normalised input itself,
+// which is what a scaling by 1 returns)
+template <int K>
+__device__ __forceinline__ cf<K> cf_scale_d(const cf<K> &a, uint32_t d) {
+  return d == 1 ? a : cf_scale_int<K>(a, d);
+}
+
 template <int L>
 __global__ void k_powers_cf(const double *__restrict__ x, int32_t n, int32_t pmax,
                             double *__restrict__ pow, const int32_t *__restrict__ status) {
@@ -103,10 +110,10 @@ __global__ void __launch_bounds__(128) k_monomials_cf(
   uint32_t wl = __ldg(occ + o0 + k - 1);
   cf<L> B = cf_ld<L>(pow + (int64_t)(wl >> 8) * WS);
   cf_st<L>(stage_val + t * WS, cf_mul<L>(F[k - 1], B));
-  cf_st<L>(stage_d + (int64_t)(o0 + k - 1) * WS, cf_scale_int<L>(F[k - 1], wl & 255u));
+  cf_st<L>(stage_d + (int64_t)(o0 + k - 1) * WS, cf_scale_d<L>(F[k - 1], wl & 255u));
   for (int s = k - 2; s >= 0; s--) {
     uint32_t w = __ldg(occ + o0 + s);
-    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_int<L>(cf_mul<L>(F[s], B), w & 255u));
+    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_d<L>(cf_mul<L>(F[s], B), w & 255u));
     if (s > 0) B = cf_mul<L>(B, cf_ld<L>(pow + (int64_t)(w >> 8) * WS));
   }
 }
@@ -239,7 +246,7 @@ __global__ void __launch_bounds__(128) k_monomials_long_cf(
   for (int s = s1 - 1; s >= s0; s--) {
     const uint32_t w = __ldg(occ + o0 + s);
     const cfo<L> g = cfo_mul<L>({cf_ld_own<L>(stage_d + (int64_t)(o0 + s) * WS), 1}, right);
-    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_int<L>(g.v, w & 255u));
+    cf_st<L>(stage_d + (int64_t)(o0 + s) * WS, cf_scale_d<L>(g.v, w & 255u));
     right = cfo_mul<L>(right, {cf_ld<L>(pow + (int64_t)(w >> 8) * WS), 1});
   }
 }
@@ -288,6 +295,49 @@ __global__ void k_sum_jacobian_cf(int64_t nz, const int32_t *__restrict__ jz_row
   for (int p = p0; p < p1; p++) cf_accumulate<L>(re, im, cf_ld<L>(stage_d + (int64_t)__ldg(jz_occ + p) * WS), E);
   const int64_t at = jz_out ? __ldg(jz_out + z) : (int64_t)__ldg(jz_col + z) * ldJ + __ldg(jz_row + z);
   cf_store_cascade<L>(J + at * 2 * L, re, im, E, false);
+}
+
+// The same sums with one warp per entry, for systems whose entries gather
+// many partials (the dense Jacobian of cyclic n-roots: up to n - 1 per
+// entry): lanes stride over the entry's partials, the largest exponent and
+// the exact aligned sum are reduced over the warp.
+template <int L>
+__global__ void __launch_bounds__(128) k_sum_jacobian_warp_cf(
+    int64_t nz, const int32_t *__restrict__ jz_row, const int32_t *__restrict__ jz_col,
+    const int32_t *__restrict__ jz_ptr, const int32_t *__restrict__ jz_occ,
+    const int64_t *__restrict__ jz_out, const double *__restrict__ stage_d, double *__restrict__ J,
+    int64_t ldJ, const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  const int64_t z = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (z >= nz || *status != GN_OK) return;  // uniform over the warp
+  const int p0 = __ldg(jz_ptr + z), p1 = __ldg(jz_ptr + z + 1);
+  int emax = CF_EZERO;
+  for (int p = p0 + lane; p < p1; p += 32) {
+    const int e = (int)(int64_t)__ldg((const uint64_t *)(stage_d + (int64_t)__ldg(jz_occ + p) * WS) + 2 * L);
+    emax = e > emax ? e : emax;
+  }
+  const int E = cf_sum_exponent(__reduce_max_sync(0xffffffffu, emax), p1 - p0);
+  fx<L + 1> re, im;
+  fx_zero<L + 1>(re);
+  fx_zero<L + 1>(im);
+  for (int p = p0 + lane; p < p1; p += 32)
+    cf_accumulate<L>(re, im, cf_ld<L>(stage_d + (int64_t)__ldg(jz_occ + p) * WS), E);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    fx<L + 1> u, v;
+#pragma unroll
+    for (int w = 0; w <= L; w++) {
+      u.w[w] = __shfl_xor_sync(0xffffffffu, re.w[w], o);
+      v.w[w] = __shfl_xor_sync(0xffffffffu, im.w[w], o);
+    }
+    re = ix_add<L + 1>(re, u);
+    im = ix_add<L + 1>(im, v);
+  }
+  if (lane == 0) {
+    const int64_t at = jz_out ? __ldg(jz_out + z) : (int64_t)__ldg(jz_col + z) * ldJ + __ldg(jz_row + z);
+    cf_store_cascade<L>(J + at * 2 * L, re, im, E, false);
+  }
 }
 
 // f_i goes to f[i], or to f[f_out[i]] (complex entries) when f_out is given
@@ -342,9 +392,14 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
     k_monomials_long_cf<L><<<(unsigned)((a.nlong + 3) / 4), 128, 0, st>>>(
         a.long_terms, a.nlong, a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val,
         a.stage_d, a.status);
-  if (a.J && a.nz > 0)
-    k_sum_jacobian_cf<L><<<(unsigned)((a.nz + 127) / 128), 128, 0, st>>>(
-        a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
+  if (a.J && a.nz > 0) {
+    if (a.nocc >= 24 * a.nz)  // many partials per entry: a warp each
+      k_sum_jacobian_warp_cf<L><<<(unsigned)((a.nz + 3) / 4), 128, 0, st>>>(
+          a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
+    else
+      k_sum_jacobian_cf<L><<<(unsigned)((a.nz + 127) / 128), 128, 0, st>>>(
+          a.nz, a.jz_row, a.jz_col, a.jz_ptr, a.jz_occ, a.jz_out, a.stage_d, a.J, a.ldJ, a.status);
+  }
   if (a.f && a.npoly > 0)
     k_sum_f_cf<L><<<(unsigned)((a.npoly + 3) / 4), 128, 0, st>>>((int32_t)a.npoly, a.poly_ptr, a.stage_val,
                                                                  a.f, a.f_out, a.neg_f, a.status);
@@ -386,6 +441,7 @@ gn_status launch_eval_int(gn_system *s, int L, const double *d_x, double *d_f, i
   a.stage_val = ws->stage_val;
   a.stage_d = ws->stage_d;
   a.nz = s->nz;
+  a.nocc = s->nnz;
   a.jz_row = s->d_jz_row;
   a.jz_col = s->d_jz_col;
   a.jz_ptr = s->d_jz_ptr;

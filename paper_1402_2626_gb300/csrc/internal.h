@@ -82,7 +82,7 @@ struct EvalArgs {
   const double *coef = nullptr;   // [4][2][T]
   const int32_t *long_terms = nullptr;  // terms with supports longer than 64 (one warp each)
   int64_t nlong = 0;
-  int64_t nz = 0;
+  int64_t nz = 0, nocc = 0;  // Jacobian entries, partials summed into them
   const int32_t *jz_row = nullptr, *jz_col = nullptr, *jz_ptr = nullptr, *jz_occ = nullptr;
   const int64_t *jz_out = nullptr;  // complex-entry offsets of the J entries (or null: col ldJ + row)
   double *J = nullptr;
