@@ -126,6 +126,7 @@ struct MfPlan {
 
 template <int L>
 static bool mf_plan(int32_t m, int32_t ncols, MfPlan<L> &p) {
+  if (ncols >= (1 << 18)) return false;  // the kernel's block indices stay below 2^16
   const int maxc = mf_max_clusters<L>(0, 0);
   if (maxc <= 0) return false;
   const int nblk = (ncols + MF_B - 1) / MF_B;

@@ -222,9 +222,16 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   const int ms = (m + MF_C - 1) / MF_C;
   const int i0 = min(m, rank * ms), i1 = min(m, i0 + ms), nr = i1 - i0;
 
-  // block-cyclic ownership: global column j <-> (owner, local index)
-  auto owner = [&](int j) { return (j / B) % G; };
-  auto lcol = [&](int j) { return ((j / B) / G) * B + (j % B); };
+  // block-cyclic ownership: global column j <-> (owner, local index).  The
+  // quotient by G (<= 152) of a block index (< 2^16) is an exact high
+  // multiply by ceil(2^32 / G): these run on the pivot chain every column.
+  static_assert(MF_B == 4, "the block index is j >> 2");
+  const uint32_t Gm = (uint32_t)((0x100000000ull + (uint64_t)G - 1) / (uint64_t)G);
+  auto owner = [&](int j) {
+    const uint32_t bj = (uint32_t)j >> 2;
+    return (int)(bj - __umulhi(bj, Gm) * (uint32_t)G);
+  };
+  auto lcol = [&](int j) { return (int)(__umulhi((uint32_t)j >> 2, Gm) * B + (j & 3)); };
   auto gcol = [&](int c) { return ((c / B) * G + g) * B + (c % B); };
   const int nblk = (ncols + B - 1) / B;
   int no = (g < nblk) ? ((nblk - g + G - 1) / G) * B : 0;  // my columns
