@@ -121,6 +121,31 @@ struct MbSite {
 // the total to every CTA (slot [rank]); the same warp of every CTA adds the 8
 // slots.  On return all lanes of the calling warps hold the totals.  A wait
 // that gives up leaves them undefined and the status word bad.
+// Exact sum over the warp of an N-limb two's-complement value (modulo
+// 2^(64N)), in every lane: each limb in four 16-bit chunks, one warp
+// reduction per chunk (sums below 2^21, so no chunk overflows), then one
+// carry pass.  The 4N reductions are independent of one another, unlike the
+// five dependent shuffle-and-add levels of a butterfly.
+template <int N>
+__device__ __forceinline__ fx<N> warp_sum_fx(const fx<N> &v) {
+  uint32_t c[4 * N];
+#pragma unroll
+  for (int w = 0; w < N; w++)
+#pragma unroll
+    for (int h = 0; h < 4; h++)
+      c[4 * w + h] = __reduce_add_sync(0xffffffffu, (uint32_t)((v.w[w] >> (16 * h)) & 0xFFFFu));
+  fx<N> r;
+  uint64_t carry = 0;
+#pragma unroll
+  for (int w = 0; w < N; w++) {
+    const u128_t a = (u128_t)carry + c[4 * w] + ((u128_t)c[4 * w + 1] << 16) +
+                     ((u128_t)c[4 * w + 2] << 32) + ((u128_t)c[4 * w + 3] << 48);
+    r.w[w] = (uint64_t)a;
+    carry = (uint64_t)(a >> 64);
+  }
+  return r;
+}
+
 template <int N, int NV>
 __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u, int rank,
                                  int32_t *status) {
@@ -131,14 +156,7 @@ __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u,
   uint64_t *sl = site.slot + (size_t)b * MF_C * SW;
   if (lane == 0) mb_expect(bar, MF_C * SW * 8);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-      fx<N> t;
-#pragma unroll
-      for (int w = 0; w < N; w++) t.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
-      v[q] = ix_add<N>(v[q], t);
-    }
+  for (int q = 0; q < NV; q++) v[q] = warp_sum_fx<N>(v[q]);
   if (lane < MF_C) {
     const uint32_t ra = cl_mapa(smem_u32(sl + (size_t)rank * SW), lane);
     const uint32_t rb = cl_mapa(smem_u32(bar), lane);
@@ -152,20 +170,8 @@ __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u,
   for (int q = 0; q < NV; q++) {
 #pragma unroll
     for (int w = 0; w < N; w++) v[q].w[w] = (lane < MF_C) ? sl[(size_t)lane * SW + q * N + w] : 0;
+    v[q] = warp_sum_fx<N>(v[q]);
   }
-#pragma unroll
-  for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-    for (int q = 0; q < NV; q++) {
-      fx<N> t;
-#pragma unroll
-      for (int w = 0; w < N; w++) t.w[w] = __shfl_xor_sync(0xffffffffu, v[q].w[w], o);
-      v[q] = ix_add<N>(v[q], t);
-    }
-#pragma unroll
-  for (int q = 0; q < NV; q++)
-#pragma unroll
-    for (int w = 0; w < N; w++) v[q].w[w] = __shfl_sync(0xffffffffu, v[q].w[w], 0);
 }
 
 // Columns per ownership block: column j belongs to cluster (j / MF_B) mod G,
@@ -434,17 +440,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
       di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      fx<K + 1> u, v;
-#pragma unroll
-      for (int w = 0; w < K + 1; w++) {
-        u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
-        v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
-      }
-      dr = ix_add<K + 1>(dr, u);
-      di = ix_add<K + 1>(di, v);
-    }
+    dr = warp_sum_fx<K + 1>(dr);
+    di = warp_sum_fx<K + 1>(di);
   };
 
   // a_j <- a_j - r q over this CTA's rows, by one warp
@@ -621,22 +618,8 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           v[0].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + w] : 0;
           v[1].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + K + 1 + w] : 0;
         }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          fx<K + 1> x, y;
-#pragma unroll
-          for (int w = 0; w < K + 1; w++) {
-            x.w[w] = __shfl_xor_sync(0xffffffffu, v[0].w[w], o);
-            y.w[w] = __shfl_xor_sync(0xffffffffu, v[1].w[w], o);
-          }
-          v[0] = ix_add<K + 1>(v[0], x);
-          v[1] = ix_add<K + 1>(v[1], y);
-        }
-#pragma unroll
-        for (int w = 0; w < K + 1; w++) {
-          v[0].w[w] = __shfl_sync(0xffffffffu, v[0].w[w], 0);
-          v[1].w[w] = __shfl_sync(0xffffffffu, v[1].w[w], 0);
-        }
+        v[0] = warp_sum_fx<K + 1>(v[0]);
+        v[1] = warp_sum_fx<K + 1>(v[1]);
         warp_axpy(q, aj, ix_narrow<K>(v[0]), ix_narrow<K>(v[1]));
         if (t > 0 && lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
         if (t == 0) {
