@@ -125,17 +125,8 @@ __device__ __forceinline__ void bt_dot(const fx<K> *q, const fx<K> *a, int N, fx
     di = ix_add<K + 1>(di, ix_mul_shift<K>(qr, ai));
     di = ix_sub<K + 1>(di, ix_mul_shift<K>(qi, ar));
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    fx<K + 1> u, v;
-#pragma unroll
-    for (int w = 0; w < K + 1; w++) {
-      u.w[w] = __shfl_xor_sync(0xffffffffu, dr.w[w], o);
-      v.w[w] = __shfl_xor_sync(0xffffffffu, di.w[w], o);
-    }
-    dr = ix_add<K + 1>(dr, u);
-    di = ix_add<K + 1>(di, v);
-  }
+  dr = warp_sum_fx<K + 1>(dr);
+  di = warp_sum_fx<K + 1>(di);
 }
 
 // a <- a - r q over the N rows
@@ -239,13 +230,7 @@ __global__ void __launch_bounds__(256) k_batch_solve(BsArgs a) {
         t = ix_add<2 * K + 1>(t, ix_square<K>(aj[2 * r]));
         t = ix_add<2 * K + 1>(t, ix_square<K>(aj[2 * r + 1]));
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        fx<2 * K + 1> u;
-#pragma unroll
-        for (int w = 0; w < 2 * K + 1; w++) u.w[w] = __shfl_xor_sync(0xffffffffu, t.w[w], o);
-        t = ix_add<2 * K + 1>(t, u);
-      }
+      t = warp_sum_fx<2 * K + 1>(t);
       if (j == n) return;  // the residual column is not normalised
       fx<K> Z;
       fx_zero<K>(Z);

@@ -404,4 +404,32 @@ FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
   }
 }
 
+#if defined(__CUDACC__)
+// Exact sum over the warp of an N-limb two's-complement value (modulo
+// 2^(64N)), in every lane: each limb in four 16-bit chunks, one warp
+// reduction per chunk (sums below 2^21, so no chunk overflows), then one
+// carry pass.  The 4N reductions are independent of one another, unlike the
+// five dependent shuffle-and-add levels of a butterfly.
+template <int N>
+__device__ __forceinline__ fx<N> warp_sum_fx(const fx<N> &v) {
+  uint32_t c[4 * N];
+#pragma unroll
+  for (int w = 0; w < N; w++)
+#pragma unroll
+    for (int h = 0; h < 4; h++)
+      c[4 * w + h] = __reduce_add_sync(0xffffffffu, (uint32_t)((v.w[w] >> (16 * h)) & 0xFFFFu));
+  fx<N> r;
+  uint64_t carry = 0;
+#pragma unroll
+  for (int w = 0; w < N; w++) {
+    const u128_t a = (u128_t)carry + c[4 * w] + ((u128_t)c[4 * w + 1] << 16) +
+                     ((u128_t)c[4 * w + 2] << 32) + ((u128_t)c[4 * w + 3] << 48);
+    r.w[w] = (uint64_t)a;
+    carry = (uint64_t)(a >> 64);
+  }
+  return r;
+}
+
+#endif
+
 }  // namespace gn
