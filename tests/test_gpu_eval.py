@@ -81,6 +81,18 @@ def test_edge_cases(prec, L, arith):
 
 @pytest.mark.parametrize("arith", ARITHS)
 @pytest.mark.parametrize("prec,L", PRECS)
+def test_support_length_boundaries(prec, L, arith):
+    """Supports of exactly k variables around the per-thread limit (64, above
+    which a warp takes a term) and around multiples of the warp's 32 lanes,
+    with exponents up to 3 (common factors inside long supports)."""
+    for k in (31, 32, 33, 63, 64, 65, 66, 95, 96, 97, 127, 128, 129, 200):
+        n = k + 8
+        sys_ = inputs.random_system(n, n, 2, k, 3, seed=1000 + k)
+        check(sys_, sys_.point("x0", L), L, prec, arith=arith)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("prec,L", PRECS)
 def test_gn32_full(prec, L, arith):
     s = inputs.workload("gn32")
     check(s, s.point("x0", L), L, prec, arith=arith)
