@@ -7,8 +7,9 @@
 // 2 us per level in DD).  Here R is cut into BSB x BSB diagonal blocks D_k:
 //   k_bs_inv        X_k = D_k^-1 for every block at once (one warp per block,
 //                   lane c forms column c by substitution inside the block);
-//   k_backsub_blk   for k = last .. 0: x_k = X_k y_k, then y_i -= R_ik x_k for
-//                   the rows above (the rows of block k-1 first).
+//   k_backsub_cl    for k = last .. 0: x_k = X_k y_k, then y_i -= R_ik x_k for
+//                   the rows above (the rows of block k-1 first), on a
+//                   cluster of CTAs.
 // Both steps of a block are small matrix-vector products: every thread forms
 // one product and 16 lanes add theirs exactly (integer sums), so a block
 // costs two products and two 4-level reductions on the chain instead of 16
@@ -169,110 +170,7 @@ __global__ void __launch_bounds__(BSB * BSB) k_bs_inv(const double *__restrict__
   cf_put<K>(Xinv + ((size_t)(k * BSB + a) * BSB + b) * CW, sX[a][b]);
 }
 
-// R x = y with y = R[0:n, n], one CTA of BSB_THREADS threads, y in shared
-// memory.  Thread t works on the pair (row r = t / 16 of the current group,
-// column c = t % 16 of the current block).
-template <int L>
-__global__ void __launch_bounds__(BSB_THREADS) k_backsub_blk(
-    const double *__restrict__ Rm, int64_t ldr, int32_t n, const double *__restrict__ sexp,
-    const double *__restrict__ Xinv, double *__restrict__ dx, int32_t *__restrict__ status) {
-  constexpr int K = L, W = 2 * L, KY = K + 2, CW = 2 * K + 1;
-  constexpr int GR = BSB_THREADS / BSB;  // rows per pass
-  extern __shared__ __align__(16) unsigned char bsm[];
-  fx<KY> *sY = (fx<KY> *)bsm;         // [n][2]
-  fx<K> *sX = (fx<K> *)(sY + 2 * n);  // [n][2]
-  int *sT = (int *)(sX + 2 * n);      // [n]
-  int *sFail = sT + n;
-  if (*status != GN_OK) return;
-  const int tid = threadIdx.x;
-  const int r = tid / BSB, c = tid % BSB;
-  const int sig = (int)sexp[n];
-  for (int i = tid; i < n; i += BSB_THREADS) {
-    const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)n * ldr + i) * W);
-    sY[2 * i] = ix_widen<K, KY>(e[0]);
-    sY[2 * i + 1] = ix_widen<K, KY>(e[1]);
-  }
-  if (tid == 0) *sFail = 0;
-  __syncthreads();
-  const int nb = (n + BSB - 1) / BSB;
-  // rows [i0, i1) -= R[rows, block k] x_block, GR rows per pass
-  auto update = [&](int k, int i0, int i1) {
-    const int b0 = k * BSB, bs = n - b0 < BSB ? n - b0 : BSB;
-    for (int base = i0; base < i1; base += GR) {
-      const int i = base + r;
-      fx<KY> ur, ui;
-      fx_zero<KY>(ur);
-      fx_zero<KY>(ui);
-      if (i < i1 && c < bs) {
-        const int j = b0 + c;
-        const fx<K> *e = (const fx<K> *)(Rm + ((int64_t)j * ldr + i) * W);
-        const int d = (int)sexp[j] + sT[j] - sig;
-        fx<KY> zr, zi;
-        fx_zero<KY>(zr);
-        fx_zero<KY>(zi);
-        bs_update<K, KY>(zr, zi, e[0], e[1], sX[2 * j], sX[2 * j + 1], d, sFail);
-        ur = zr;  // = -R_ij x_j in units of y
-        ui = zi;
-      }
-#pragma unroll
-      for (int o = 8; o > 0; o >>= 1) {
-        fx<KY> a, b;
-#pragma unroll
-        for (int w = 0; w < KY; w++) {
-          a.w[w] = __shfl_xor_sync(0xffffffffu, ur.w[w], o);
-          b.w[w] = __shfl_xor_sync(0xffffffffu, ui.w[w], o);
-        }
-        ur = ix_add<KY>(ur, a);
-        ui = ix_add<KY>(ui, b);
-      }
-      if (c == 0 && i < i1) {
-        sY[2 * i] = ix_add<KY>(sY[2 * i], ur);
-        sY[2 * i + 1] = ix_add<KY>(sY[2 * i + 1], ui);
-      }
-    }
-  };
-  for (int k = nb - 1; k >= 0; k--) {
-    const int b0 = k * BSB, bs = n - b0 < BSB ? n - b0 : BSB;
-    // x_k = X_k y_k: pair (row b0 + r, column b0 + c).  Whole warps (the
-    // first BSB rows of pairs) take part in the group sums, with has = false
-    // past the block's size.
-    if (r < BSB) {
-      const bool has = r < bs && c >= r && c < bs;
-      cf<K> p = cf_zero<K>();
-      if (has) {
-        const cf<K> xk = cf_get<K>(Xinv + ((size_t)(k * BSB + r) * BSB + c) * CW);
-        const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
-        p = cf_mul<K>(xk, yc);
-      }
-      const cf<K> s = cf_group16_sum<K>(p, has);
-      if (c == 0 && r < bs) {
-        sX[2 * (b0 + r)] = s.re;
-        sX[2 * (b0 + r) + 1] = s.im;
-        sT[b0 + r] = s.e;
-      }
-    }
-    __syncthreads();
-    if (k > 0) {
-      update(k, b0 - BSB, b0);  // the next block's rows first
-      update(k, 0, b0 - BSB);
-    }
-    __syncthreads();
-  }
-  if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
-  for (int l = tid; l < n; l += BSB_THREADS) {
-    double cr[L], ci[L];
-    const bool z = sT[l] == CF_EZERO;
-    fx_to_cascade<K, L>(sX[2 * l], z ? 0 : -sT[l], cr);
-    fx_to_cascade<K, L>(sX[2 * l + 1], z ? 0 : -sT[l], ci);
-#pragma unroll
-    for (int q = 0; q < L; q++) {
-      dx[(int64_t)l * W + q] = cr[q];
-      dx[(int64_t)l * W + L + q] = ci[q];
-    }
-  }
-}
-
-// The same solve on a cluster of BSC CTAs: block b of rows (and of y) lives
+// R x = y with y = R[0:n, n] on a cluster of BSC CTAs: block b of rows (and of y) lives
 // in CTA b mod BSC.  Per block k, from the last: the owner of block k-1
 // subtracts R_(k-1),k x_k from its rows and forms x_(k-1) = X_(k-1) y_(k-1)
 // at once, storing it into every CTA's shared memory (double-buffered by the
@@ -542,11 +440,6 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_fwdsub_cl(
     cl.sync();
   }
   if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
-}
-
-template <int L>
-__host__ __device__ constexpr size_t bsb_smem_bytes(int n) {
-  return (sizeof(fx<L + 2>) * 2 + sizeof(fx<L>) * 2 + sizeof(int)) * (size_t)(n > 0 ? n : 1) + 16;
 }
 
 template <int L>

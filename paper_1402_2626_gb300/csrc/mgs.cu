@@ -267,8 +267,8 @@ static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const doub
                             cudaStream_t st) {
   const double *sexp = rinv + (size_t)(n + 1) * L + (n + 1);
   const int nb = (n + BSB - 1) / BSB;
-  k_bs_inv<L><<<(unsigned)nb, BSB * BSB, 0, st>>>(Rm, ldr, n, Zs, sexp, Xinv, status);
   if (bsc_available<L>()) {
+    k_bs_inv<L><<<(unsigned)nb, BSB * BSB, 0, st>>>(Rm, ldr, n, Zs, sexp, Xinv, status);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(BSC);
     cfg.blockDim = dim3(BSB_THREADS);
@@ -286,13 +286,7 @@ static gn_status bsb_launch(const double *Rm, int64_t ldr, int32_t n, const doub
       return GN_ECUDA;
     return GN_OK;
   }
-  const size_t bytes = bsb_smem_bytes<L>(n);
-  if (bytes > 48 * 1024 &&
-      cudaFuncSetAttribute(k_backsub_blk<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-          cudaSuccess)
-    return GN_ECUDA;
-  k_backsub_blk<L><<<1, BSB_THREADS, bytes, st>>>(Rm, ldr, n, sexp, Xinv, dx, status);
-  return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
+  return bs_launch<L>(Rm, ldr, n, Zs, rinv, dx, status, st);  // no cluster: one level at a time
 }
 
 // the same for the forward substitution of the adjoint
