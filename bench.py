@@ -45,9 +45,17 @@ FP64_PEAK_GINSTR = 2 * 152 * 2.070
 # 2070 MHz, in G lane-instructions/s.
 IMAD_PEAK_GINSTR = 64 * 152 * 2.070
 PRECS = {"d": 1, "dd": 2, "qd": 4}
-# kernels one Gauss-Newton step launches (integer arithmetic): k_powers,
-# k_monomials, k_sum_jacobian, k_sum_f, k_mgs_int, k_backsub_int, k_update
-LAUNCHES_PER_STEP = 7
+# DRAM bytes (read + write) of one k_mgs_int launch inside the gn256 Newton
+# step, from the ncu launch list of the current kernel
+# (profiles/gn256_dd_newton_launches.md: 2.305 MB read, 0 written, mean of 9
+# launches), by limbs; a precision without such a capture reports null
+MGS_TRAFFIC = {2: 2.305e6}
+# untimed steps run just before the timed region while the clocks are sampled
+SOAK_S = 1.0
+# kernels one Gauss-Newton step launches at n = 256 (integer arithmetic):
+# k_powers_cf, k_monomials_cf, k_sum_jacobian_cf, k_sum_f_cf, k_mgs_int,
+# k_bs_inv and k_backsub_cl (the blocked back substitution), k_update
+LAUNCHES_PER_STEP = 8
 
 # FP64 instructions (DADD, DMUL, DFMA each one) per complex operation of the
 # device arithmetic in csrc/mw.cuh, counted from the source.
@@ -118,7 +126,9 @@ def job_throughput(world: int, steps: int, t_max: float) -> float:
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms; each sample
+    is stamped on arrival, and only those inside the marked region count (the
+    timed steps and the untimed run of the same steps just before them)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -127,50 +137,61 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = None
+        self.lines = []
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.perf_counter(), line))
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(suffix=".csv")
-        os.close(fd)
+        import threading
         try:
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=self.fh, stderr=subprocess.DEVNULL)
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except Exception:
             self.proc = None
+            return
+        self.reader = threading.Thread(target=self._read, daemon=True)
+        self.reader.start()
+
+    def region(self, t0: float, t1: float):
+        """The timed region, in time.perf_counter() seconds."""
+        self.t0, self.t1 = t0, t1
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         if self.proc is None:
             return out
-        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
+        self.reader.join(timeout=5)
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as fh:
-            for line in fh:
-                p = [q.strip() for q in line.split(",")]
-                if len(p) < 9:
-                    continue
-                try:
-                    sm.append(float(p[1]))
-                    mx.append(float(p[2]))
-                except ValueError:
-                    continue
-                for nm, flag in zip(names, p[5:9]):
-                    if flag.lower() == "active":
-                        reasons.add(nm)
-        os.unlink(self.path)
+        for ts, line in list(self.lines):
+            if self.t0 is not None and not (self.t0 <= ts <= self.t1):
+                continue
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, flag in zip(names, p[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(nm)
         if sm:
             out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
                    "reasons": sorted(reasons), "samples": len(sm)}
+        if self.t0 is not None:
+            out["window_s"] = self.t1 - self.t0
         return out
 
 
@@ -326,6 +347,16 @@ def main():
         clocks.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
+    # the same steps, untimed, for ~1 s just before the timed region, so
+    # that the 200 ms clock samples see the GPU under this load (a timed
+    # region of a few tens of ms falls between two samples)
+    t_soak = time.perf_counter()
+    while time.perf_counter() - t_soak < SOAK_S:
+        for _ in range(10):
+            flush.zero_()
+            x.copy_(x0)
+            step()
+        torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -336,6 +367,7 @@ def main():
         step()
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    clocks.region(t_soak, time.perf_counter())
     if dist:
         dist.barrier()
     clk = clocks.stop() if rank == 0 else {}
@@ -717,8 +749,7 @@ def breakdown(S, system, dev, flush, args):
                     "bound": "alu", "achieved": achieved, "peak": IMAD_PEAK_GINSTR,
                     "unit": "G IMAD/s", "frac": achieved / IMAD_PEAK_GINSTR,
                     "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2.07 GHz",
-                    # ncu, one DD launch inside the Newton step (k_mgs_int_dd_gn256.md)
-                    "traffic": 2.27e6 if L == 2 else None,
+                    "traffic": MGS_TRAFFIC.get(L),
                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch",
                     "algorithmic_imad": work, "launch_ms": t_mgs,
                     "us_per_column": 1e3 * t_mgs / (system.n + 1),

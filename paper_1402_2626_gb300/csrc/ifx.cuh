@@ -348,6 +348,106 @@ FX_HD void ix_rsqrt_step(const ux<K> &tt, ux<K> &Y) {
   for (int i = 0; i < K; i++) Y.w[i] = Yf.w[i];
 }
 
+// One higher-order step in K limbs (scale S = 64K - 2): with e = 1 - t y^2,
+// 1/sqrt(t) = y (1 - e)^(-1/2) = y (1 + e/2 + 3e^2/8 + 5e^3/16 + ...), so
+// y <- y (1 + e/2 + 3e^2/8 + 5e^3/16) leaves a relative error of about
+// (35/128) e^4: from |e| <= 2^-36 (one 1-limb Newton step from a seed good
+// to 2^-20) below 2^-145, from |e| <= 2^-100 (a 2-limb result) far below
+// 2^-256; under one unit of the result either way, where Newton would need
+// two steps.  EB: the step applies when |e| < 2^-EB (else returns false and
+// leaves Y as it was).  e^2 and e^3 are formed from the 64 bits of |e| below
+// 2^(S-EB): eh = |e| / 2^(S-EB-64), e^2 / 2^S = eh^2 / 2^(2EB+128-S) (error
+// below 2^(S-2EB-63) units), e^3 / 2^(2S) = (e^2 / 2^S) eh / 2^(EB+64).
+template <int K, int EB>
+FX_HD bool ix_rsqrt_step3(const ux<K> &tt, ux<K> &Y) {
+  constexpr int S = 64 * K - 2;
+  constexpr int LO = S - EB - 64;          // eh = |e| >> LO
+  constexpr int SH = 2 * EB + 128 - S;     // e^2 / 2^S = eh^2 >> SH
+  static_assert(LO >= 0 && SH >= 64 && SH < 128, "guard out of range");
+  // W = Y^2 / 2^S (K+1 limbs), V = t W / 2^(64K), e = 2^S - V: as in ix_rsqrt_step
+  const ux<2 * K> y2 = ix_umul<K>(Y, Y);
+  ux<K + 1> Wv;
+#pragma unroll
+  for (int t = 0; t <= K; t++) {
+    const uint64_t lo = y2.w[K - 1 + t] >> 62;
+    const uint64_t hi = (K + t < 2 * K) ? (y2.w[K + t] << 2) : 0;
+    Wv.w[t] = lo | hi;
+  }
+  ux<K> Wk;
+#pragma unroll
+  for (int i = 0; i < K; i++) Wk.w[i] = Wv.w[i];
+  const ux<2 * K> tw = ix_umul<K>(tt, Wk);
+  ux<K> V;
+#pragma unroll
+  for (int i = 0; i < K; i++) V.w[i] = tw.w[K + i];
+  {
+    u128_t c = 0;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+      c += (u128_t)V.w[i] + (u128_t)tt.w[i] * Wv.w[K];
+      V.w[i] = (uint64_t)c;
+      c >>= 64;
+    }
+  }
+  fx<K> one, Vf;
+#pragma unroll
+  for (int i = 0; i < K; i++) {
+    one.w[i] = (i == (S >> 6)) ? (1ull << (S & 63)) : 0;
+    Vf.w[i] = V.w[i];
+  }
+  const fx<K> e = ix_sub<K>(one, Vf);
+  uint64_t ne;
+  const ux<K> ue = ix_abs<K>(e, ne);
+  // |e| < 2^(S-EB): no bit at or above S - EB
+  {
+    uint64_t hi = 0;
+#pragma unroll
+    for (int i = 0; i < K; i++) {
+      const int b0 = 64 * i;  // limb i holds bits b0 .. b0 + 63
+      if (b0 + 63 >= S - EB) hi |= (b0 >= S - EB) ? ue.w[i] : (ue.w[i] >> ((S - EB) - b0));
+    }
+    if (hi) return false;
+  }
+  // eh = bits LO .. LO + 63 of |e|
+  uint64_t eh;
+  {
+    const int li = LO >> 6, lb = LO & 63;
+    eh = ue.w[li] >> lb;
+    if (lb && li + 1 < K) eh |= ue.w[li + 1] << (64 - lb);
+  }
+  const uint64_t e2 = (uint64_t)(((u128_t)eh * eh) >> SH);  // < 2^(128 - SH)
+  const uint64_t e3 = (uint64_t)(((u128_t)e2 * eh) >> (EB + 64));  // < 2^(S - 2EB)
+  // c = e/2 + 3 e^2 / 8 + 5 e^3 / 16 (signed, scale 2^S)
+  fx<K> c = ix_sar<K>(e, 1);
+  fx<K> t3, t5;
+#pragma unroll
+  for (int i = 0; i < K; i++) t3.w[i] = t5.w[i] = 0;
+  t3.w[0] = (3 * e2) >> 3;
+  t5.w[0] = (5 * e3) >> 4;
+  ix_cneg<K>(t5, ne);
+  c = ix_add<K>(c, t3);
+  c = ix_add<K>(c, t5);
+  uint64_t nc;
+  const ux<K> uc = ix_abs<K>(c, nc);
+  // Y <- Y + Y c / 2^S; Y c / 2^S = bits S .. S + 64K - 1 of the product
+  const ux<2 * K> yc = ix_umul<K>(Y, uc);
+  fx<K> d;
+#pragma unroll
+  for (int t = 0; t < K; t++) {
+    const uint64_t lo = yc.w[K - 1 + t] >> 62;
+    const uint64_t hi = yc.w[K + t] << 2;
+    d.w[t] = lo | hi;
+  }
+  ix_cneg<K>(d, nc);
+  fx<K> Yf;
+#pragma unroll
+  for (int i = 0; i < K; i++) Yf.w[i] = Y.w[i];
+  Yf = ix_add<K>(Yf, d);
+#pragma unroll
+  for (int i = 0; i < K; i++) Y.w[i] = Yf.w[i];
+  return true;
+}
+
 // the top KK limbs of tt, and Y from KK to 2 KK limbs (same value)
 template <int K, int KK>
 FX_HD ux<KK> ix_top(const ux<K> &tt) {
@@ -365,14 +465,44 @@ FX_HD ux<2 * KK> ix_rsqrt_widen(const ux<KK> &Y) {
   return r;
 }
 
+// The steps after the seed: Y1 = y0 2^62 with y0 ~ 1/sqrt(t) to 2^-20 or
+// better (one limb at scale 2^62; FP32 rsqrtf is within 2^-21.8).
+template <int K>
+FX_HD ux<K> ix_rsqrt_from_seed(const ux<K> &tt, ux<1> Y1) {
+  static_assert(K == 1 || K == 2 || K == 4, "K = 1, 2 or 4 limbs");
+  const ux<1> t1 = ix_top<K, 1>(tt);
+  ix_rsqrt_step<1>(t1, Y1);  // ~43 bits
+  if constexpr (K == 1) {
+    ix_rsqrt_step<1>(t1, Y1);
+    return Y1;
+  } else {
+    ux<2> Y2 = ix_rsqrt_widen<1>(Y1);
+    const ux<2> t2 = ix_top<K, 2>(tt);
+    if (!ix_rsqrt_step3<2, 36>(t2, Y2)) {  // ~128 bits; else two Newton steps
+      ix_rsqrt_step<2>(t2, Y2);
+      ix_rsqrt_step<2>(t2, Y2);
+    }
+    if constexpr (K == 2) {
+      return Y2;
+    } else {
+      ux<4> Y4 = ix_rsqrt_widen<2>(Y2);
+      if (!ix_rsqrt_step3<4, 100>(tt, Y4)) {  // ~256 bits
+        ix_rsqrt_step<4>(tt, Y4);
+        ix_rsqrt_step<4>(tt, Y4);
+      }
+      return Y4;
+    }
+  }
+}
+
 // Y = 2^(64K-2) / sqrt(t) for t = tt / 2^(64K) in [1/4, 1), tt a K-limb
-// unsigned fraction: FP32 reciprocal square root seed (24 bits), then Newton
-// steps, each in as many limbs as its result needs: 1 limb (48 bits), then
-// 1 more (K = 1) or 2 limbs (96 bits), then K limbs until K limbs are full.
+// unsigned fraction: FP32 reciprocal square root seed (24 bits), then steps
+// in as many limbs as their result needs: a Newton step in 1 limb (~43 bits),
+// then one more (K = 1), or a third-order step in 2 limbs (~128 bits) and,
+// for K = 4, a third-order step in 4 limbs.
 // Y is in (2^(64K-2), 2^(64K-1)].
 template <int K>
 FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
-  static_assert(K == 1 || K == 2 || K == 4, "K = 1, 2 or 4 limbs");
   // seed from the top 32 bits of t
   const float tf = (float)(uint32_t)(tt.w[K - 1] >> 32) * 2.3283064365386963e-10f;  // 2^-32
 #if defined(__CUDA_ARCH__)
@@ -383,25 +513,7 @@ FX_HD ux<K> ix_rsqrt_frac(const ux<K> &tt) {
   // y0 in (1, 2] with 24 significant bits, as one limb at scale 2^62
   ux<1> Y1;
   Y1.w[0] = (uint64_t)(y0 * 16777216.0f) << 38;
-  const ux<1> t1 = ix_top<K, 1>(tt);
-  ix_rsqrt_step<1>(t1, Y1);  // ~48 bits
-  if constexpr (K == 1) {
-    ix_rsqrt_step<1>(t1, Y1);
-    return Y1;
-  } else {
-    ux<2> Y2 = ix_rsqrt_widen<1>(Y1);
-    const ux<2> t2 = ix_top<K, 2>(tt);
-    ix_rsqrt_step<2>(t2, Y2);  // ~96 bits
-    if constexpr (K == 2) {
-      ix_rsqrt_step<2>(t2, Y2);
-      return Y2;
-    } else {
-      ux<4> Y4 = ix_rsqrt_widen<2>(Y2);
-      ix_rsqrt_step<4>(tt, Y4);  // ~192 bits
-      ix_rsqrt_step<4>(tt, Y4);
-      return Y4;
-    }
-  }
+  return ix_rsqrt_from_seed<K>(tt, Y1);
 }
 
 #if defined(__CUDACC__)

@@ -1,7 +1,7 @@
 // Host harness for csrc/ifx.cuh (test support).  Reads lines
 // "op K a_0..a_{K-1} b_0..b_{K-1} [s]" (hex limbs, little-endian) and prints
 // the result limbs in hex.  ops: mul (ix_mul_shift), sq (ix_square),
-// add, sub, sar (by s), bitlen; and "xsar N a_0..a_{N-1} s" / "xshl N ..."
+// add, sub, sar (by s), bitlen, rsqrt, rsqrtseed (with a given seed); and "xsar N a_0..a_{N-1} s" / "xshl N ..."
 // (ix_sar / ix_shl on N-limb values, N = 1..5 or 9).
 #include <cstdio>
 #include <cstring>
@@ -34,6 +34,16 @@ static void run(const char *op) {
     gn::ux<K> t;
     for (int i = 0; i < K; i++) t.w[i] = a.w[i];
     gn::ux<K> y = gn::ix_rsqrt_frac<K>(t);
+    for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)y.w[i]);
+  } else if (!strcmp(op, "rsqrtseed")) {
+    // t in a, then the one-limb seed Y1 (scale 2^62)
+    gn::ux<K> t;
+    for (int i = 0; i < K; i++) t.w[i] = a.w[i];
+    unsigned long long y1;
+    scanf("%llx", &y1);
+    gn::ux<1> Y1;
+    Y1.w[0] = y1;
+    gn::ux<K> y = gn::ix_rsqrt_from_seed<K>(t, Y1);
     for (int i = 0; i < K; i++) printf("%llx ", (unsigned long long)y.w[i]);
   } else if (!strcmp(op, "mulf")) {
     // a (K+1 limbs: a_0..a_{K-1} then one more) times b (K limbs)

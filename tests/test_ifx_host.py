@@ -147,3 +147,30 @@ def test_rsqrt_frac(harness, K):
         # exact: floor(2^S * sqrt(2^(64K) / t)) = isqrt(2^(2S + 64K) // t)
         want = math.isqrt((1 << (2 * S + 64 * K)) // t)
         assert abs(Y - want) <= 8, (K, t, Y - want)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_rsqrt_from_any_seed_within_ulps(harness, K):
+    """The steps after the seed reach Y = 2^(64K-2)/sqrt(t) to within a few units
+    from every FP32 seed within 8 ulp (2^-20) of 1/sqrt(t): the device's rsqrtf
+    is within 2 ulp, the host's 1/sqrtf within 1."""
+    import math
+    rng = np.random.default_rng(90 + K)
+    ts = [1 << (64 * K - 2), (1 << (64 * K)) - 1, (1 << (64 * K - 1)) + 1]
+    for _ in range(150):
+        v = int.from_bytes(rng.bytes(8 * K), "little")
+        ts.append((v >> 2) | (1 << (64 * K - 2)))
+    S = 64 * K - 2
+    lines, want = [], []
+    for t in ts:
+        # y = 2^(32K)/sqrt(t) in (1, 2]; its 24-bit grid is y 2^23
+        g = math.isqrt((1 << (64 * K + 46)) // t)
+        exact = math.isqrt((1 << (2 * S + 64 * K)) // t)
+        for m in (-8, -3, -2, -1, 0, 1, 2, 3, 8):
+            seed = (g + m) << 39
+            lines.append(f"rsqrtseed {K} " + " ".join("%x" % x for x in limbs(t, K) + [0] * K)
+                         + " %x" % seed)
+            want.append(exact)
+    for w, got in zip(want, run(harness, lines)):
+        Y = val(got, signed=False)
+        assert abs(Y - w) <= 8, (K, Y - w)
