@@ -47,9 +47,9 @@ IMAD_PEAK_GINSTR = 64 * 152 * 2.070
 PRECS = {"d": 1, "dd": 2, "qd": 4}
 # DRAM bytes (read + write) of one k_mgs_int launch inside the gn256 Newton
 # step, from the ncu launch list of the current kernel
-# (profiles/gn256_dd_newton_launches.md: 2.305 MB read, 0 written, mean of 9
+# (profiles/gn256_dd_newton_launches.md: 2.311 MB read, 0 written, mean of 19
 # launches), by limbs; a precision without such a capture reports null
-MGS_TRAFFIC = {2: 2.305e6}
+MGS_TRAFFIC = {2: 2.311e6}
 # untimed steps run just before the timed region while the clocks are sampled
 SOAK_S = 1.0
 # kernels one Gauss-Newton step launches at n = 256 (integer arithmetic):

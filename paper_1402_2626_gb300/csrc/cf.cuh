@@ -36,26 +36,43 @@ FX_HD cf<K> cf_zero() {
   return z;
 }
 
+// the low K limbs of floor(x / 2^(r - 8)) for a signed (K+1)-limb x with
+// |x| < 2^(64K + 55) and 0 <= r < 64: x 2^8 (exact), then one funnel shift
+// right by r (a shift left by 8 - r when r < 8); no branch on the direction
+template <int K>
+FX_HD fx<K> cf_shift8(const fx<K + 1> &x, int r) {
+  fx<K + 1> t;
+#pragma unroll
+  for (int i = 0; i <= K; i++) t.w[i] = (x.w[i] << 8) | (i > 0 ? x.w[i - 1] >> 56 : 0);
+  fx<K> o;
+#pragma unroll
+  for (int i = 0; i < K; i++) o.w[i] = (t.w[i] >> r) | ((t.w[i + 1] << 1) << (63 - r));
+  return o;
+}
+
 // shift a (K+1)-limb signed value so that max bit length lands on 64K-2,
 // then narrow to K limbs; returns the exponent adjustment
 template <int K>
 FX_HD int cf_normalize(fx<K + 1> &re, fx<K + 1> &im, fx<K> &ore, fx<K> &oim) {
   uint64_t n1, n2;
   const ux<K + 1> ur = ix_abs<K + 1>(re, n1), ui = ix_abs<K + 1>(im, n2);
-  fx<K + 1> ar, ai;
+  // the bit length of max(|re|, |im|) is that of |re| | |im|
+  fx<K + 1> am;
 #pragma unroll
-  for (int w = 0; w <= K; w++) {
-    ar.w[w] = ur.w[w];
-    ai.w[w] = ui.w[w];
-  }
-  const int b1 = ix_bitlen<K + 1>(ar), b2 = ix_bitlen<K + 1>(ai);
-  const int B = b1 > b2 ? b1 : b2;
+  for (int w = 0; w <= K; w++) am.w[w] = ur.w[w] | ui.w[w];
+  const int B = ix_bitlen<K + 1>(am);
   if (B == 0) {
     fx_zero<K>(ore);
     fx_zero<K>(oim);
     return CF_EZERO;
   }
   const int sh = B - (64 * K - 2);  // > 0: shift right
+  if (sh >= -8 && sh < 56) {
+    // every normalised product, scaling and conversion lands here
+    ore = cf_shift8<K>(re, sh + 8);
+    oim = cf_shift8<K>(im, sh + 8);
+    return sh;
+  }
   if (sh >= 0) {
     re = ix_sar<K + 1>(re, sh);
     im = ix_sar<K + 1>(im, sh);

@@ -416,7 +416,9 @@ FX_HD bool ix_rsqrt_step3(const ux<K> &tt, ux<K> &Y) {
     if (lb && li + 1 < K) eh |= ue.w[li + 1] << (64 - lb);
   }
   const uint64_t e2 = (uint64_t)(((u128_t)eh * eh) >> SH);  // < 2^(128 - SH)
-  const uint64_t e3 = (uint64_t)(((u128_t)e2 * eh) >> (EB + 64));  // < 2^(S - 2EB)
+  // e2 eh < 2^118: for EB + 64 >= 128 (the 4-limb step) the term is zero
+  uint64_t e3 = 0;  // < 2^(S - 2EB)
+  if constexpr (EB + 64 < 128) e3 = (uint64_t)(((u128_t)e2 * eh) >> (EB + 64));
   // c = e/2 + 3 e^2 / 8 + 5 e^3 / 16 (signed, scale 2^S)
   fx<K> c = ix_sar<K>(e, 1);
   fx<K> t3, t5;
