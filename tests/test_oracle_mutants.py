@@ -59,6 +59,15 @@ MUTANTS = [
     ("exponent ignored in the monomial values",
      "for (int r = 0; r < exp[o]; r++) c_mul(L, acc, x + (int64_t)var[o] * W, acc);",
      "for (int r = 0; r < 1; r++) c_mul(L, acc, x + (int64_t)var[o] * W, acc);"),
+    ("projection added instead of subtracted in the MGS update",
+     "        c_mul(L, r, ak + i * W, p);\n        c_sub(L, aj + i * W, p, aj + i * W);",
+     "        c_mul(L, r, ak + i * W, p);\n        c_add(L, aj + i * W, p, aj + i * W);"),
+    ("pivot norm as a^T a instead of a^H a",
+     "      x_grow_prod(&e, a[L + i], a[L + j]);\n    }\n  x_round(&e, L, r);",
+     "      x_grow_prod(&e, -a[L + i], a[L + j]);\n    }\n  x_round(&e, L, r);"),
+    ("power table squares instead of multiplying by x",
+     "        c_mul(L, pow_tab + ((int64_t)v * pmax + p - 2) * W, xv(&cx, v),",
+     "        c_mul(L, pow_tab + ((int64_t)v * pmax + p - 2) * W, pow_tab + ((int64_t)v * pmax + p - 2) * W,"),
     ("update subtracts instead of adds",
      "for (int i = 0; i < n; i++) c_add(L, x + i * W, dx + i * W, x + i * W);",
      "for (int i = 0; i < n; i++) c_sub(L, x + i * W, dx + i * W, x + i * W);"),
