@@ -86,11 +86,24 @@ FX_HD int cf_normalize(fx<K + 1> &re, fx<K + 1> &im, fx<K> &ore, fx<K> &oim) {
   return sh;
 }
 
-// a * b
+// a * b.  Each part is the same value as the difference (sum) of the two
+// signed truncated products ix_mul_shift forms, s1 T1 -+ s2 T2, taken as
+// s1 (T1 -+ s1 s2 T2) on the magnitudes T: one addition with a conditional
+// complement and one conditional negation instead of two negations and an
+// addition.
 template <int K>
 FX_HD cf<K> cf_mul(const cf<K> &a, const cf<K> &b) {
-  fx<K + 1> re = ix_sub<K + 1>(ix_mul_shift<K>(a.re, b.re), ix_mul_shift<K>(a.im, b.im));
-  fx<K + 1> im = ix_add<K + 1>(ix_mul_shift<K>(a.re, b.im), ix_mul_shift<K>(a.im, b.re));
+  uint64_t nar, nai, nbr, nbi;
+  const ux<K> uar = ix_abs<K>(a.re, nar), uai = ix_abs<K>(a.im, nai);
+  const ux<K> ubr = ix_abs<K>(b.re, nbr), ubi = ix_abs<K>(b.im, nbi);
+  // re = s_rr T_rr - s_ii T_ii = s_rr (T_rr - s_rr s_ii T_ii)
+  const uint64_t srr = nar ^ nbr, sii = nai ^ nbi;
+  fx<K + 1> re = ix_add_cneg<K + 1>(ix_umul_shift<K>(uar, ubr), ix_umul_shift<K>(uai, ubi), 1 ^ srr ^ sii);
+  ix_cneg<K + 1>(re, srr);
+  // im = s_ri T_ri + s_ir T_ir = s_ri (T_ri + s_ri s_ir T_ir)
+  const uint64_t sri = nar ^ nbi, sir = nai ^ nbr;
+  fx<K + 1> im = ix_add_cneg<K + 1>(ix_umul_shift<K>(uar, ubi), ix_umul_shift<K>(uai, ubr), sri ^ sir);
+  ix_cneg<K + 1>(im, sri);
   cf<K> r;
   const int sh = cf_normalize<K>(re, im, r.re, r.im);
   r.e = (sh == CF_EZERO || a.e == CF_EZERO || b.e == CF_EZERO) ? CF_EZERO

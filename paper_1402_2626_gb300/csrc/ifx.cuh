@@ -114,6 +114,37 @@ FX_HD fx<K + 1> ix_mul_shift(const fx<K> &a, const fx<K> &b) {
   return r;
 }
 
+// |a| |b| / 2^(64K - 2) truncated, for unsigned K-limb |a|, |b|: the
+// magnitude ix_mul_shift negates (K+1 limbs)
+template <int K>
+FX_HD fx<K + 1> ix_umul_shift(const ux<K> &ua, const ux<K> &ub) {
+  const ux<2 * K> p = ix_umul<K>(ua, ub);
+  fx<K + 1> r;
+#pragma unroll
+  for (int t = 0; t <= K; t++) {
+    const uint64_t lo = p.w[K - 1 + t] >> 62;
+    const uint64_t hi = (K + t < 2 * K) ? (p.w[K + t] << 2) : 0;
+    r.w[t] = lo | hi;
+  }
+  return r;
+}
+
+// a + b when neg = 0, a - b when neg = 1 (N limbs, mod 2^(64N)): b's
+// complement and the carry-in of its +1 go into the one addition
+template <int N>
+FX_HD fx<N> ix_add_cneg(const fx<N> &a, const fx<N> &b, uint64_t neg) {
+  const uint64_t m = 0 - neg;
+  fx<N> r;
+  u128_t c = neg;
+#pragma unroll
+  for (int i = 0; i < N; i++) {
+    c += (u128_t)a.w[i] + (u128_t)(b.w[i] ^ m);
+    r.w[i] = (uint64_t)c;
+    c >>= 64;
+  }
+  return r;
+}
+
 // a * b exactly for signed KA- and KB-limb values, as KA+KB limbs (signed)
 template <int KA, int KB>
 FX_HD fx<KA + KB> ix_mul_full(const fx<KA> &a, const fx<KB> &b) {
