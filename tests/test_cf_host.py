@@ -102,3 +102,16 @@ def test_scale_and_round_trip(harness, K, L):
         gr, gi = cval(got, L)
         err = cabs(gr - d * ar, gi - d * ai)
         assert err <= 8 * BOUND[L] * d * cabs(ar, ai) + (0 if ar or ai else 0), (kind, K, err)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4])
+def test_fast_forms_bit_identical(harness, K):
+    """The renormalisation (one bit length of |re| | |im|, a branch-free shift for
+    shifts of -8..55 bits) and the product (each part as one addition with a
+    conditional complement and one conditional negation) equal, bit for bit,
+    their written-out forms: separate left and right barrel shifts, and four
+    signed truncated products added and subtracted."""
+    n = 100000 if K < 4 else 50000
+    out = subprocess.run([harness], input=f"same {K} {n} {1234567 + K}\n", capture_output=True,
+                         text=True, check=True).stdout.split()
+    assert out == ["ok", str(n)], out
