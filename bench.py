@@ -162,37 +162,44 @@ class ClockSampler:
         self.t0, self.t1 = t0, t1
 
     def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         if self.proc is None:
-            return out
+            return summarize_clocks([], None, None)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.reader.join(timeout=5)
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ts, line in list(self.lines):
-            if self.t0 is not None and not (self.t0 <= ts <= self.t1):
-                continue
-            p = [q.strip() for q in line.split(",")]
-            if len(p) < 9:
-                continue
-            try:
-                sm.append(float(p[1]))
-                mx.append(float(p[2]))
-            except ValueError:
-                continue
-            for nm, flag in zip(names, p[5:9]):
-                if flag.lower() == "active":
-                    reasons.add(nm)
-        if sm:
-            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
-                   "reasons": sorted(reasons), "samples": len(sm)}
-        if self.t0 is not None:
-            out["window_s"] = self.t1 - self.t0
-        return out
+        return summarize_clocks(list(self.lines), self.t0, self.t1)
+
+
+def summarize_clocks(lines, t0, t1):
+    """Median SM clock, maximum clock and throttle reasons of the stamped
+    nvidia-smi lines (FIELDS order) that fall in [t0, t1] (all of them when
+    t0 is None)."""
+    out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ts, line in lines:
+        if t0 is not None and not (t0 <= ts <= t1):
+            continue
+        p = [q.strip() for q in line.split(",")]
+        if len(p) < 9:
+            continue
+        try:
+            sm.append(float(p[1]))
+            mx.append(float(p[2]))
+        except ValueError:
+            continue
+        for nm, flag in zip(names, p[5:9]):
+            if flag.lower() == "active":
+                reasons.add(nm)
+    if sm:
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+               "reasons": sorted(reasons), "samples": len(sm)}
+    if t0 is not None:
+        out["window_s"] = t1 - t0
+    return out
 
 
 def oracle_steps(system, L, nsteps, nthreads):
