@@ -89,3 +89,50 @@ def term_scales(system, x, rows=None):
             for v, d in zip(vs, ds):
                 SJ[i - r0, v] += d * mag / ax[v]
     return Sf, SJ
+
+
+def lstsq_sensitivity(A, Ro):
+    """First-order perturbation factors of one least-squares case.
+
+    Both sides of a parity test run modified Gram-Schmidt, which is backward
+    stable: each result is the exact factorisation of [A b] moved by a
+    relative amount of order u_L, far below the stated tolerance tol_L.  The
+    difference of the two results therefore obeys the standard first-order
+    perturbation bounds with eps = tol_L, with the condition number kappa of
+    A = [A b][:, :n] read from the oracle's R (same singular values as A):
+
+      column j of R (b's column included):  |dr_kj| <= eps kappa ||a_j||
+      column k < n of Q:                    |dq_ik| <= eps kappa
+      solution x of min ||A x - b||:
+          ||dx|| <= eps kappa (||x|| + (||b|| + kappa ||r||) / sigma_max)
+
+    (R and Q: the sensitivity of the QR factors; x: the Golub-Van Loan /
+    Wedin bound for least squares, r = b - A x, ||r|| = r_nn from MGS).
+    Returns (kappa, column norms of [A b], the factor of eps for x).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    Ro = np.asarray(Ro, dtype=np.float64)
+    n = Ro.shape[0] - 1
+    cn = np.sqrt((A[..., 0] ** 2).sum(axis=(0, 2)))  # ||a_j|| (double, leading limbs)
+    Rc = Ro[:n, :n, 0, 0] + 1j * Ro[:n, :n, 1, 0]
+    sv = np.linalg.svd(Rc, compute_uv=False)
+    kappa = float(sv[0] / sv[-1])
+    y = Ro[:n, n, 0, 0] + 1j * Ro[:n, n, 1, 0]
+    x = np.linalg.solve(np.triu(Rc), y)
+    rnorm = float(abs(Ro[n, n, 0, 0] + 1j * Ro[n, n, 1, 0]))
+    fx = kappa * (float(np.linalg.norm(x)) + (float(cn[n]) + kappa * rnorm) / float(sv[0]))
+    return kappa, cn, fx
+
+
+def rounding_residual_scale(system, x, rows=None):
+    """Per-row scale of |f_i(x)| at a computed root x.
+
+    A root carried to relative accuracy eps in each component leaves, to
+    first order, |f_i(x)| <= eps (S_f[i] + sum_v S_J[i, v] |x_v|): the
+    evaluation's own rounding (S_f) plus the change of f under a relative
+    move eps |x_v| of each variable (S_J the Jacobian's term scales).
+    """
+    Sf, SJ = term_scales(system, x, rows=rows)
+    x = np.asarray(x)
+    ax = np.abs(x[:, 0, 0] + 1j * x[:, 1, 0])
+    return Sf + SJ @ ax
