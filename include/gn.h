@@ -49,7 +49,7 @@ typedef enum {
   GN_ECUDA = 3,      /* a CUDA runtime call failed */
   GN_ESINGULAR = 4,  /* rank-deficient Jacobian: r_kk <= 2^(8-50L) ||a_k|| */
   GN_ENOCONV = 5,    /* tolerance not reached within the allowed steps */
-  GN_ENONFINITE = 6, /* NaN or Inf in f, J or the update */
+  GN_ENONFINITE = 6, /* NaN or Inf in the inputs (x, coefficients, [A b]), f, J or the update */
   GN_ETIMEOUT = 7    /* a bounded device-side wait gave up */
 } gn_status;
 
@@ -144,7 +144,8 @@ gn_status gn_eval(gn_system *s, gn_prec prec, const double *d_x, double *d_f,
  *   d_dx : [n] complex, output: the least-squares solution of A dx = b.
  * Returns GN_ESINGULAR (after synchronizing) when a pivot r_kk, k < n, is at
  * most 2^(8-50L) times the original norm of column k (under GN_ARITH_INT the
- * test compares bit lengths, so the threshold holds within a factor of 2).
+ * test compares bit lengths, so the threshold holds within a factor of 2),
+ * and GN_ENONFINITE when [A b] holds a NaN or an infinity.
  */
 gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
                    int64_t ldAb, double *d_R, double *d_dx, void *cuda_stream);
@@ -154,7 +155,8 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
  * (Section 3, eq. 2) without the back substitution, fully stream-ordered.
  *   d_Ab, ldAb, d_R : as for gn_lstsq (Q and b - Q y overwrite d_Ab; R into d_R).
  *   d_status : device int32 the caller owns; when the kernels finish it holds
- *              GN_OK, GN_ESINGULAR (the rank test of gn_lstsq) or GN_ETIMEOUT.
+ *              GN_OK, GN_ESINGULAR (the rank test of gn_lstsq), GN_ENONFINITE
+ *              (a NaN or an infinity in [A b]) or GN_ETIMEOUT.
  * Requires n <= the system's number of variables (it uses the system's
  * workspace).  Does not synchronize: check *d_status after the stream does.
  */
@@ -172,7 +174,9 @@ gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab,
  *   tol    : 0 to always take `steps` steps; > 0 to stop early, GN_ENOCONV if
  *            never reached.
  *   report : host-owned, may be NULL.
- * Synchronizes the stream before returning.
+ * Synchronizes the stream before returning.  A step that fails (GN_ESINGULAR;
+ * GN_ENONFINITE for a NaN or an infinity in x or a coefficient, which
+ * reaches f and J; GN_ETIMEOUT) leaves x as the previous step left it.
  */
 gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, double tol,
                     gn_report *report, void *cuda_stream);
@@ -305,16 +309,24 @@ gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps,
  * library routine.  Its scratch is one static device array of
  * GN_NOALLOC_SCRATCH_BYTES inside the library, which every process that
  * loads the library holds on each GPU it uses until it exits.
- *   It always evaluates with GN_ARITH_FP64 arithmetic.
+ *   It always evaluates with the GN_ARITH_FP64 kernels (cascades combined
+ *   by error-free transformations), whatever gn_system_set_arith chose; the
+ *   results meet the accuracy stated for gn_eval.
  *   Arguments, layouts and outputs are those of gn_eval; d_x, d_f and d_J
  *   remain caller memory and the system must already be loaded (loading it
- *   allocates).
- *   Returns GN_EINVAL when the scratch the system needs — 256 bytes plus
- *   16 * prec bytes per power-table entry (n x max(dmax-1, 1)), per term (T)
- *   and per variable occurrence (nnz), each part rounded up to 256 bytes —
- *   exceeds GN_NOALLOC_SCRATCH_BYTES.
+ *   allocates).  Like gn_eval it is stream-ordered, does not synchronize and
+ *   reports no device-side condition: a NaN or infinite input comes out as
+ *   NaN or infinite entries of f and J.
+ *   Returns GN_EINVAL for a system with a monomial of more than 64
+ *   variables (gn_eval accepts those, e.g. cyclic n-roots for n > 64), and
+ *   when the scratch the system needs — 256 bytes plus 16 * prec bytes per
+ *   power-table entry (n x max(dmax-1, 1)), per term (T) and per variable
+ *   occurrence (nnz), each part rounded up to 256 bytes — exceeds
+ *   GN_NOALLOC_SCRATCH_BYTES.
  *   The first call on a device looks up the scratch address on that device
- *   (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   (cudaGetSymbolAddress) and loads the kernels of all three precisions
+ *   (under lazy module loading a kernel's first launch may allocate); make
+ *   that first call, in any precision, before any stream capture.
  *   All calls share the one array and it keeps the last call's contents:
  *   calls whose work overlaps on the GPU (other streams, other host threads)
  *   race on it and must be serialized by the caller.
@@ -323,6 +335,25 @@ gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps,
 #define GN_NOALLOC_SCRATCH_BYTES (64u << 20)
 gn_status gn_eval_noalloc(const gn_system *s, gn_prec prec, const double *d_x, double *d_f,
                           double *d_J, int64_t ldJ, void *cuda_stream);
+
+/*
+ * Bound of one device-side wait of the MGS kernel (the cluster reductions
+ * and the pivot flags of Section 3's factorisation, which the kernel runs
+ * as one persistent launch), in SM clock cycles, on the current device.
+ * A wait that runs out records GN_ETIMEOUT in the call's status word; every
+ * other wait of the launch then gives up at once and the kernel returns, so
+ * a lost message costs about one bound and leaves the device usable.
+ *   cycles   : > 0 sets the bound; 0 restores the default (2e9 cycles,
+ *              about one second at the GB300's clock).
+ *   previous : host int64, may be NULL: the bound before this call.
+ * Applies to launches issued after the call (also replays of captured
+ * Newton graphs, which read the bound when they run).  Not stream-ordered:
+ * change it while no factorisation is in flight.  Returns GN_EINVAL for
+ * cycles < 0, GN_ECUDA if the device copy cannot be read or written.
+ * For tests of the failure path and for callers that prefer a prompt
+ * GN_ETIMEOUT over a long wait; the paper has no counterpart.
+ */
+gn_status gn_set_wait_limit(int64_t cycles, int64_t *previous);
 
 /* Human-readable name of a status. */
 const char *gn_status_str(gn_status st);

@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(256) k_batch_solve(BsArgs a) {
       for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
       if (lane == 0) {
         const double n0 = sqrt(t);
+        if (!isfinite(n0)) sFail = 1;  // a NaN or an infinity in the column
         const int sj = fx_exponent_of(n0 * 1.0000001 + 1e-300) - S;
         sS[c] = sj;
         sTb[c] = 2 * (fx_exponent_of(n0) - 1 + 8 - 50 * L - sj) + 1;
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(256) k_batch_solve(BsArgs a) {
         const int bl = ix_bitlen<2 * K + 1>(t);
         b = (bl + 1) >> 1;
         accept = bl > sTb[j];
-        if (!accept) sFail = 2;
+        if (!accept && !sFail) sFail = 2;  // a non-finite input is reported as such
         ux<K> tt;
         const int d = 2 * b - 64 * K;
         const fx<2 * K + 1> sh = d >= 0 ? ix_sar<2 * K + 1>(t, d) : ix_shl<2 * K + 1>(t, -d);

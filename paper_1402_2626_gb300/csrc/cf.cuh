@@ -21,6 +21,15 @@ namespace gn {
 
 constexpr int CF_EZERO = -(1 << 28);  // exponent of zero
 
+// Exponent of a value that stands for a NaN or an infinity (cf_from_cascade
+// of a non-finite input).  Products stay at or near it (cf_mul saturates
+// there), sums align to it and drop every finite term, and cf_store_cascade
+// writes NaN for it, so a non-finite input reaches f and J as NaN, as it
+// would in floating point; one that meets an exact zero factor vanishes.
+// Finite values stay far below it (|e| < 2^17 for values in the double
+// range and products of a few hundred of them).
+constexpr int CF_ENAN = 1 << 24;
+
 template <int K>
 struct cf {
   fx<K> re, im;
@@ -106,8 +115,8 @@ FX_HD cf<K> cf_mul(const cf<K> &a, const cf<K> &b) {
   ix_cneg<K + 1>(im, sri);
   cf<K> r;
   const int sh = cf_normalize<K>(re, im, r.re, r.im);
-  r.e = (sh == CF_EZERO || a.e == CF_EZERO || b.e == CF_EZERO) ? CF_EZERO
-                                                                 : a.e + b.e + (64 * K - 2) + sh;
+  const int e = a.e + b.e + (64 * K - 2) + sh;
+  r.e = (sh == CF_EZERO || a.e == CF_EZERO || b.e == CF_EZERO) ? CF_EZERO : (e < CF_ENAN ? e : CF_ENAN);
   return r;
 }
 
@@ -140,6 +149,17 @@ FX_HD cf<K> cf_scale_int(const cf<K> &a, uint32_t d) {
 // from the [re limbs | im limbs] cascade of L doubles
 template <int K, int L>
 FX_HD cf<K> cf_from_cascade(const double (&re)[L], const double (&im)[L]) {
+  bool finite = true;
+#pragma unroll
+  for (int l = 0; l < L; l++) finite &= isfinite(re[l]) && isfinite(im[l]);
+  if (!finite) {
+    cf<K> z;  // any normalised mantissas, exponent CF_ENAN
+    fx_zero<K>(z.re);
+    fx_zero<K>(z.im);
+    z.re.w[K - 1] = z.im.w[K - 1] = 1ull << 61;
+    z.e = CF_ENAN;
+    return z;
+  }
   const double m = fabs(re[0]) > fabs(im[0]) ? fabs(re[0]) : fabs(im[0]);
   if (!(m > 0.0)) return cf_zero<K>();
   // |value| < 2^(E+1) with E the exponent of the leading limb (one bit of

@@ -200,16 +200,30 @@ constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mutex;
 static unsigned char *g_noalloc_ptr[kMaxDevices];  // device address of the scratch, per device
 
+// the kernels of gn_eval_noalloc at precision L, loaded now: under lazy
+// module loading (the CUDA default) a kernel's code is loaded, which may
+// allocate device memory, at its first launch, and that first launch may be
+// a later call in another precision
+template <int L>
+static bool noalloc_load_kernels() {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, k_powers<L>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fa, k_monomials<L>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fa, k_sum_jacobian<L>) == cudaSuccess &&
+         cudaFuncGetAttributes(&fa, k_sum_f<L>) == cudaSuccess;
+}
+
 // Host code must not hand g_noalloc_scratch to a kernel: on the host that
 // name is a stand-in, not a device address.  Look the address up once per
-// device, with that device current.
+// device, with that device current, and load the kernels of every precision.
 static gn_status noalloc_scratch(unsigned char **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GN_ECUDA;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
   if (!g_noalloc_ptr[dev]) {
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+        !noalloc_load_kernels<1>() || !noalloc_load_kernels<2>() || !noalloc_load_kernels<4>()) {
       cudaGetLastError();
       return GN_ECUDA;
     }
@@ -237,7 +251,10 @@ static gn_status eval_noalloc_impl(const gn_system *s, const double *d_x, double
   double *pow = (double *)(base + b_status);
   double *stage_val = (double *)(base + b_status + b_pow);
   double *stage_d = (double *)(base + b_status + b_pow + b_val);
-  // the scratch keeps the previous call's contents: the status word must start at 0
+  // The scratch keeps the previous call's contents.  The status word only
+  // gates the kernels (each returns at once on a bad status, none sets one),
+  // so it must start at GN_OK; like gn_eval, the call reports no device-side
+  // condition (a NaN input comes out as NaN in f and J).
   if (cudaMemsetAsync(status, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return GN_ECUDA;
   k_powers<L><<<(s->n + 127) / 128, 128, 0, st>>>(d_x, s->n, s->pmax, pow, status);
   if (s->T > 0)

@@ -258,6 +258,9 @@ __device__ __forceinline__ void cf_store_cascade(double *dst, const fx<L + 1> &r
   if (E == CF_EZERO) {
 #pragma unroll
     for (int l = 0; l < L; l++) r[l] = i[l] = 0.0;
+  } else if (E > CF_ENAN / 2) {  // a non-finite input reached this sum
+#pragma unroll
+    for (int l = 0; l < L; l++) r[l] = i[l] = __longlong_as_double(0x7FF8000000000000ll);
   } else {
     fx_to_cascade<L + 1, L>(re, 64 - E, r);
     fx_to_cascade<L + 1, L>(im, 64 - E, i);

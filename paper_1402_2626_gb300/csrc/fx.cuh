@@ -221,8 +221,12 @@ FX_HD void fx_to_cascade(fx<NL> a, int F, double (&out)[L]) {
       E += 1;
     }
     const int biased = E + 1075;
-    if (biased <= 0 || biased >= 2047) {
-      out[l] = 0.0;  // outside the normal range: not produced by the scales used here
+    if (biased <= 0) {
+      out[l] = 0.0;  // below the normal range: not produced by the scales used here
+      continue;
+    }
+    if (biased >= 2047) {
+      out[l] = fx_bitsd(0x7FF8000000000000ull);  // beyond the double range: NaN
       continue;
     }
     out[l] = fx_bitsd((sign << 63) | ((uint64_t)biased << 52) | (m & 0xFFFFFFFFFFFFFull));

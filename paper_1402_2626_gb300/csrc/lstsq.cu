@@ -58,7 +58,7 @@ __device__ cx<L> block_sum(cx<L> v, cx<L> *sh /* >= 32 entries */) {
 // Double estimates of the original column norms, for the rank test.
 template <int L>
 __global__ void k_colnorms(const double *__restrict__ A, int32_t m, int64_t lda, int32_t ncols,
-                           double *__restrict__ nrm0) {
+                           double *__restrict__ nrm0, int32_t *__restrict__ status) {
   int j = blockIdx.x;
   if (j >= ncols) return;
   double s = 0.0;
@@ -75,6 +75,8 @@ __global__ void k_colnorms(const double *__restrict__ A, int32_t m, int64_t lda,
     double t = 0.0;
     for (int w = 0; w < (int)((blockDim.x + 31) >> 5); w++) t += sh[w];
     nrm0[j] = sqrt(t);
+    // a NaN or an infinity in the column, reported before any pivot runs
+    if (!isfinite(t)) atomicCAS(status, GN_OK, GN_ENONFINITE);
   }
 }
 
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(MGS_THREADS) k_mgs_pivot(double *__restrict__ 
     for (int l = 0; l < L; l++) rc.re[l] = r.v[l];
     c_store<L>(R + ((int64_t)k * ldr + k) * W, rc);
     int ok = 1;
-    if (!isfinite(r.v[0])) {
+    if (!isfinite(ss.v[0]) || !isfinite(r.v[0])) {
       ok = 0;
       atomicCAS(status, GN_OK, GN_ENONFINITE);
     } else if (k < ncols - 1) {
@@ -269,7 +271,7 @@ static gn_status lstsq_impl(bool use_int, int32_t m, int32_t n, double *A, int64
   }
   if (cudaMemsetAsync(R, 0, sizeof(double) * 2 * L * ldr * ncols, st) != cudaSuccess) return GN_ECUDA;
   // one launch per pivot and one per trailing update (devices without clusters)
-  k_colnorms<L><<<ncols, 128, 0, st>>>(A, m, lda, ncols, nrm0);
+  k_colnorms<L><<<ncols, 128, 0, st>>>(A, m, lda, ncols, nrm0, status);
   for (int k = 0; k < ncols; k++) {
     k_mgs_pivot<L><<<1, MGS_THREADS, 0, st>>>(A, m, lda, ncols, k, R, ldr, rinv, nrm0, status);
     if (k < ncols - 1)

@@ -23,9 +23,10 @@
 //     normalisation by a step so blocks would not read a half-normalised
 //     column; here the flags give that ordering inside one launch.
 //
-// Every wait is bounded (about one second); a wait that gives up records
-// GN_ETIMEOUT, later waits see the bad status and give up at once, and every
-// CTA of the cluster leaves together, so no CTA is left at a cluster barrier.
+// Every wait is bounded (about one second by default, gn_set_wait_limit); a
+// wait that gives up records GN_ETIMEOUT, later waits see the bad status and
+// give up at once, and every CTA of the cluster leaves together, so no CTA
+// is left at a cluster barrier.
 #include <cooperative_groups.h>
 
 #include <mutex>
@@ -43,7 +44,12 @@ namespace gn {
 constexpr int MF_THREADS = 256;
 constexpr int MF_WARPS = MF_THREADS / 32;
 constexpr int MF_C = 8;                         // CTAs per cluster
-constexpr long long MF_WAIT_CYCLES = 2000000000LL;  // bound of one wait (~1 s)
+constexpr long long MF_WAIT_CYCLES = 2000000000LL;  // default bound of one wait (~1 s)
+
+// Bound of one device-side wait in SM clock cycles, read by every launch of
+// k_mgs_int at its start (so captured graphs see a changed value on their
+// next replay).  gn_set_wait_limit changes it on the current device.
+__device__ long long g_mf_wait_cycles = MF_WAIT_CYCLES;
 constexpr size_t MF_SMEM_FLOOR = 120 * 1024;    // keeps one CTA per SM
 
 struct MfArgs {
@@ -436,3 +442,21 @@ gn_status launch_mgs_flow(int L, double *A, int32_t m, int64_t lda, int32_t ncol
 }
 
 }  // namespace gn
+
+extern "C" gn_status gn_set_wait_limit(int64_t cycles, int64_t *previous) {
+  if (cycles < 0) return GN_EINVAL;
+  long long old = 0;
+  if (previous) {
+    if (cudaMemcpyFromSymbol(&old, gn::g_mf_wait_cycles, sizeof(old)) != cudaSuccess) {
+      cudaGetLastError();
+      return GN_ECUDA;
+    }
+    *previous = old;
+  }
+  const long long v = cycles == 0 ? gn::MF_WAIT_CYCLES : (long long)cycles;
+  if (cudaMemcpyToSymbol(gn::g_mf_wait_cycles, &v, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return GN_ECUDA;
+  }
+  return GN_OK;
+}

@@ -50,10 +50,11 @@ __device__ __forceinline__ void st_async8(uint32_t ra, uint64_t v, uint32_t rb) 
 
 // Wait until the phase of parity par of a local mbarrier has completed
 // (acquire at cluster scope: the stores that completed it are visible).
-// Gives up after about a second (recording GN_ETIMEOUT), or soon after the
+// Gives up after g_mf_wait_cycles (recording GN_ETIMEOUT), or soon after the
 // status word turns bad; returns whether the phase completed.
 __device__ __forceinline__ bool mb_wait(uint64_t *bar, uint32_t par, int32_t *status) {
   const uint32_t a = smem_u32(bar);
+  const long long lim = g_mf_wait_cycles;  // consumed only once the wait spins
   const long long t0 = clock64();
   for (uint32_t it = 0;; it++) {
     uint32_t done;
@@ -66,7 +67,7 @@ __device__ __forceinline__ bool mb_wait(uint64_t *bar, uint32_t par, int32_t *st
         : "memory");
     if (done) return true;
     if ((it & 15) == 15 && *(volatile int32_t *)status != GN_OK) return false;
-    if (clock64() - t0 > MF_WAIT_CYCLES) {
+    if (clock64() - t0 > lim) {
       atomicCAS(status, GN_OK, GN_ETIMEOUT);
       return false;
     }
@@ -264,6 +265,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     double t = 0.0;
     for (int r = 0; r < MF_C; r++) t += cl.map_shared_rank(sN0p, r)[c];
     const double n0 = sqrt(t);
+    // a NaN or an infinity anywhere in the column: every CTA of the owner
+    // cluster sees it here, before any pivot could record a rank deficiency
+    if (!isfinite(n0)) atomicCAS(a.status, GN_OK, GN_ENONFINITE);
     sN0[c] = n0;
     const int sj = fx_exponent_of(n0 * 1.0000001 + 1e-300) - S;
     sS[c] = sj;
@@ -546,6 +550,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       int okv = 1;
       if (tid == 0) {
         const uint32_t *f = a.flags + (size_t)k * MF_C + rank;
+        const long long lim = g_mf_wait_cycles;
         const long long t0 = clock64();
         uint32_t v;
         for (;;) {
@@ -555,7 +560,7 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
             v = 2;
             break;
           }
-          if (clock64() - t0 > MF_WAIT_CYCLES) {
+          if (clock64() - t0 > lim) {
             atomicCAS(a.status, GN_OK, GN_ETIMEOUT);
             v = 2;
             break;

@@ -35,7 +35,7 @@ REPORT_MAX = 64
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
            "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_batch_create", "gn_batch_destroy",
            "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc",
-           "gn_system_set_coef", "gn_adjoint", "gn_newton_mixed")
+           "gn_system_set_coef", "gn_adjoint", "gn_newton_mixed", "gn_set_wait_limit")
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
@@ -105,6 +105,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_batch_info.restype = C.c_int
         L.gn_batch_newton.argtypes = [vp, C.c_int, vp, C.c_int32, vp, vp, vp]
         L.gn_batch_newton.restype = C.c_int
+        L.gn_set_wait_limit.argtypes = [C.c_int64, i64p]
+        L.gn_set_wait_limit.restype = C.c_int
         L.gn_status_str.argtypes = [C.c_int]
         L.gn_status_str.restype = C.c_char_p
         L.gn_version.restype = C.c_int32
@@ -303,6 +305,16 @@ class Batch:
         _check(self._lib.gn_batch_newton(self._h, PREC[prec], _ptr(x), steps, _ptr(norms),
                                          C.c_void_p(status.data_ptr()), _stream(stream)),
                "gn_batch_newton")
+
+
+def set_wait_limit(cycles: int) -> int:
+    """Bound of one device-side wait of the MGS kernel in SM clock cycles on
+    the current device (0 restores the default); returns the previous bound
+    (gn_set_wait_limit)."""
+    L = load_library()
+    prev = C.c_int64()
+    _check(L.gn_set_wait_limit(int(cycles), C.byref(prev)), "gn_set_wait_limit")
+    return prev.value
 
 
 _root_fn = None

@@ -52,25 +52,34 @@ def test_noalloc_matches_gn_eval_twice(prec, L):
         s.close()
 
 
-def test_noalloc_allocates_nothing():
+@pytest.mark.parametrize("warm_prec,warm_L", [("dd", 2), ("d", 1)])
+def test_noalloc_allocates_nothing(warm_prec, warm_L):
+    """After one first call in one precision, calls in every precision leave
+    the device's free memory unchanged (the first call also loads the code of
+    the other precisions' kernels)."""
     gn = _gn()
     warm = inputs.random_system(4, 4, 4, (1, 3), 3, seed=1)
     w = gn.System(warm)
-    xw = torch.tensor(warm.point("x0", 2), device="cuda")
-    w.eval_noalloc("dd", xw)  # first call on the device: loads code, looks up the scratch
+    xw = torch.tensor(warm.point("x0", warm_L), device="cuda")
+    w.eval_noalloc(warm_prec, xw)  # first call on the device: looks up the scratch
     torch.cuda.synchronize()
     system = inputs.workload("gn32")
     s = gn.System(system)  # loading the system allocates; evaluating must not
-    x = torch.tensor(system.point("x0", 2), device="cuda")
-    f, J = _buffers(system, 2)
+    bufs = {}
+    for prec, L in PRECS:
+        x = torch.tensor(system.point("x0", L), device="cuda")
+        bufs[prec] = (x, *_buffers(system, L))
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
-    for _ in range(3):
-        s.eval_noalloc("dd", x, f, J)
+    for _ in range(2):
+        for prec, _L in PRECS:
+            x, f, J = bufs[prec]
+            s.eval_noalloc(prec, x, f, J)
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free1 == free0
-    assert not torch.isnan(J).any()
+    for prec, _L in PRECS:
+        assert not torch.isnan(bufs[prec][2]).any()
     s.close()
     w.close()
 
