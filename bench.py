@@ -37,19 +37,18 @@ METRIC = "complex DD/QD monomial eval+diff/s; Newton steps/s; % of FP64 peak vs 
 UNIT = "Newton steps/s"
 WORKLOAD = "gn256"
 L2_BYTES = 129 * 2 ** 20
-# FP64 issue rate: 2 FP64 lanes per clock per SM (the nominal 1.25 TFLOP/s
-# FMA rate of GB300) x 152 SMs x 2070 MHz, in G lane-instructions/s.
-FP64_PEAK_GINSTR = 2 * 152 * 2.070
-# 32-bit integer multiply-add issue rate: 64 IMAD lanes per clock per SM (half
-# the 128 FP32 lanes; 19 T lane-ops/s measured on this part) x 152 SMs x
-# 2070 MHz, in G lane-instructions/s.
-IMAD_PEAK_GINSTR = 64 * 152 * 2.070
+# Issue rates per SM per clock of the pipes the kernels use: 2 FP64 lanes
+# (GB300's nominal 1.25 TFLOP/s FMA rate over 152 SMs at 2070 MHz) and 64
+# 32-bit IMAD lanes (half the 128 FP32 lanes).  Peaks are these times the
+# device's SM count and maximum SM clock (device_peaks); the probes in
+# probe/rates.cu measure the same pipes (measured_rates).
+FP64_LANES_PER_SM = 2
+IMAD_LANES_PER_SM = 64
 PRECS = {"d": 1, "dd": 2, "qd": 4}
-# DRAM bytes (read + write) of one k_mgs_int launch inside the gn256 Newton
-# step, from the ncu launch list of the current kernel
-# (profiles/gn256_dd_newton_launches.md: 2.311 MB read, 0 written, mean of 19
-# launches), by limbs; a precision without such a capture reports null
-MGS_TRAFFIC = {2: 2.311e6}
+# DRAM bytes (read + write) of one k_mgs_int launch at 256 x 257, by limbs,
+# from a one-kernel ncu capture of the current kernel (null: no capture of
+# the current kernel at that precision)
+MGS_TRAFFIC = {}
 # untimed steps run just before the timed region while the clocks are sampled
 SOAK_S = 1.0
 # kernels one Gauss-Newton step launches at n = 256 (integer arithmetic):
@@ -99,6 +98,60 @@ def algorithmic_imad_mgs(m, ncols, L):
     pairs = ncols * (ncols - 1) // 2
     real_products = ncols * 4 * m + pairs * 8 * m
     return real_products * 4 * L * L
+
+
+def device_peaks(dev):
+    """FP64 and IMAD issue peaks (G lane-instructions/s) of the device: lanes
+    per SM per clock x SMs (read from the device) x maximum SM clock (from
+    nvidia-smi, else the GB300's 2070 MHz)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, src = 2070.0, "GB300 maximum (nvidia-smi unavailable)"
+    try:
+        out = subprocess.run(["nvidia-smi", f"--id={torch.cuda.current_device()}",
+                              "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip()
+        mhz, src = float(out.splitlines()[0]), "nvidia-smi clocks.max.sm"
+    except Exception:
+        pass
+    ghz = mhz / 1e3
+    return {"sms": sms, "sm_max_mhz": mhz, "clock_source": src,
+            "fp64_ginstr": FP64_LANES_PER_SM * sms * ghz, "imad_ginstr": IMAD_LANES_PER_SM * sms * ghz,
+            "derivation": f"lanes/clk/SM x {sms} SMs x {mhz:.0f} MHz "
+                          f"(FP64 {FP64_LANES_PER_SM}, IMAD {IMAD_LANES_PER_SM})"}
+
+
+def measured_hbm_gbs() -> float:
+    """The machine's measured copy bandwidth (GB/s) when the driver wrote it,
+    else the fallback figure of one earlier GB300 measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
+def measured_rates():
+    """Issue rates of the FP64 FMA, FP64 tensor (DMMA), IMAD and FP32 FMA pipes
+    measured by the probes of probe/rates.cu on this device (one launch each
+    of about 20-60 ms, after one warm-up launch)."""
+    import ctypes as C
+
+    from paper_1402_2626_gb300 import build
+
+    lib = C.CDLL(build.PROBE_LIB)
+    lib.gn_probe_rate.argtypes = [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                  C.POINTER(C.c_double)]
+    out = {}
+    for which, name, iters, unit in ((0, "fp64_fma", 20000, "G lane-op/s"),
+                                     (1, "dmma_fp64", 5000, "GFLOP/s"),
+                                     (2, "imad", 400000, "G lane-op/s"),
+                                     (3, "fp32_fma", 600000, "G lane-op/s")):
+        rate, ms = C.c_double(), C.c_double()
+        st = lib.gn_probe_rate(which, 4, iters, C.byref(rate), C.byref(ms))
+        out[name] = {"rate": rate.value, "unit": unit, "ms": ms.value} if st == 0 else {"error": st}
+    return out
 
 
 def rank_system(rank: int):
@@ -215,6 +268,53 @@ def oracle_steps(system, L, nsteps, nthreads):
     return times
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+
+    return platform.machine()
+
+
+def oracle_parts(system, L, cores):
+    """The oracle's evaluation (reverse mode: common factor and sequential
+    Speelpenning; definition mode: every partial by direct powering) and MGS
+    least squares, each timed at one thread (the paper timed one core) and
+    at all cores, on bounded samples scaled to the whole system: evaluation
+    on a block of rows (its time is proportional to the rows), MGS whole."""
+    import oracle
+
+    x = system.point("x0", L)
+    out = {}
+    for mode, rows1, rows_all in (("reverse", 32, system.N), ("definition", 8, 64)):
+        row = {}
+        for threads, rows in ((1, rows1), (cores, rows_all)):
+            rows = min(rows, system.N)
+            t = time.perf_counter()
+            oracle.evaluate(system, x, L, mode, rows=(0, rows), nthreads=threads)
+            dt = time.perf_counter() - t
+            row[f"{threads}_thread_ms"] = 1e3 * dt * system.N / rows
+            row[f"{threads}_thread_sample_rows"] = rows
+        out[f"eval_{mode}"] = row
+    f, J, _ = oracle.evaluate(system, x, L, "reverse", nthreads=cores)
+    A = oracle.augmented(f, J)
+    mg = {}
+    for threads in (cores, 1):
+        t = time.perf_counter()
+        oracle.mgs(A, L, nthreads=threads)
+        mg[f"{threads}_thread_ms"] = 1e3 * (time.perf_counter() - t)
+    out["mgs"] = mg
+    one = out["eval_reverse"]["1_thread_ms"] + mg["1_thread_ms"]
+    out["newton_steps_per_s_1_thread"] = 1e3 / one
+    return out
+
+
 def cpu_baseline(system, L, budget_s=15.0):
     import oracle
 
@@ -226,7 +326,8 @@ def cpu_baseline(system, L, budget_s=15.0):
         times.extend(oracle_steps(system, L, 1, cores))
     return {"value": len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{len(times)} full Gauss-Newton steps of the {WORKLOAD} workload in "
-                      f"{ {1: 'D', 2: 'DD', 4: 'QD'}[L]} ({sum(times):.1f} s)"}
+                      f"{ {1: 'D', 2: 'DD', 4: 'QD'}[L]} ({sum(times):.1f} s)",
+            "cpu": cpu_model(), "parts": oracle_parts(system, L, cores)}
 
 
 def cpu_adjoint_baseline():
@@ -257,7 +358,7 @@ def run_section(args):
     fn = {"adjoint": lambda: adjoint_extra(dev, flush, args),
           "mixed": lambda: mixed_extra(dev, flush, args),
           "paper": lambda: paper_extra(dev, flush, args),
-          "batched": lambda: batched(dev, args)}[args.only]
+          "batched": lambda: batched(dev, args, device_peaks(dev))}[args.only]
     print(json.dumps({"section": args.only, args.only: fn()}), flush=True)
     return 0
 
@@ -402,17 +503,27 @@ def main():
 
     extras = {}
     roofline = None
+    head = {}
     if rank == 0 and not args.no_extras:
-        extras, roofline = breakdown(S, system, dev, flush, args)
+        peaks = device_peaks(dev)
+        peaks["hbm_gbs"] = measured_hbm_gbs()
+        rates = measured_rates()
+        extras, roofline = breakdown(S, system, dev, flush, args, peaks, rates)
+        # the evaluation half of the metric, first in the line
+        head["eval_diff_monomials_per_s"] = {
+            p: {"int": extras["eval_diff"][p]["int"]["monomials_per_s"],
+                "fp64": extras["eval_diff"][p]["fp64"]["monomials_per_s"]} for p in PRECS}
+        extras["peaks"] = peaks
+        extras["measured_rates"] = rates
         extras["adjoint"] = adjoint_extra(dev, flush, args)
         extras["mixed"] = mixed_extra(dev, flush, args)
         extras["paper_workloads"] = paper_extra(dev, flush, args)
         if not args.no_batch:
-            extras["batched"] = batched(dev, args)
+            extras["batched"] = batched(dev, args, peaks)
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": value, "unit": UNIT, **head, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": 1e3 * t_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
@@ -616,12 +727,11 @@ def adjoint_extra(dev, flush, args):
             "loss": "sum |x_j|^2 at the root (g = 2x)"}
 
 
-def batched(dev, args, loop_sample=64):
+def batched(dev, args, peaks):
     """The batched configuration: 4096 independent systems (n in [16, 128],
     M in [n/2, 2n] per polynomial, k in [2, 16], exponents 1..4), complex DD,
     one graph per Newton step; against the same systems stepped one at a time
-    through the single-system path (measured on ``loop_sample`` systems spread
-    over the sizes, scaled to the batch)."""
+    through the single-system path (gn_newton on each system in turn)."""
     import numpy as np
     import torch
 
@@ -652,41 +762,59 @@ def batched(dev, args, loop_sample=64):
     step_ms = statistics.median(ms)
     ok = not bool(status.any().item())
     g.close()
-    # the plain path, one system at a time, on systems spread over the sizes
-    order = np.argsort(b.n, kind="stable")
-    pick = order[np.linspace(0, b.S - 1, loop_sample).astype(int)]
-    loop_ms = []
-    for s in pick:
-        sy = b.system(int(s))
+    # the plain path, one system at a time, over every system of the batch:
+    # each system is loaded and its step captured first (untimed), then one
+    # gn_newton step of each, back to back, timed as a whole (each call
+    # synchronizes to read its status, as a user's loop would)
+    t_load = time.perf_counter()
+    plain = []
+    for s in range(b.S):
+        sy = b.system(s)
         S1 = gn.System(sy)
         xs0 = torch.tensor(sy.point("x0", L), device=dev)
         xs = xs0.clone()
-        S1.newton("dd", xs, 1)  # captures its step
-        xs.copy_(xs0)
+        S1.newton("dd", xs, 1)  # allocates the workspace, captures the step
+        plain.append((S1, xs0, xs))
+    load_s = time.perf_counter() - t_load
+    loop_ms = []
+    for _ in range(2):
+        for _S1, xs0, xs in plain:
+            xs.copy_(xs0)
         torch.cuda.synchronize()
-        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        S1.newton("dd", xs, 1)
-        e.record(stream)
+        t = time.perf_counter()
+        for S1, _xs0, xs in plain:
+            S1.newton("dd", xs, 1)
         torch.cuda.synchronize()
-        loop_ms.append(a.elapsed_time(e))
+        loop_ms.append(1e3 * (time.perf_counter() - t))
+    for S1, _xs0, _xs in plain:
         S1.close()
-    loop_total_ms = float(np.mean(loop_ms)) * b.S
+    loop_total_ms = min(loop_ms)
     imad = sum(algorithmic_imad_mgs(int(n), int(n) + 1, L) for n in b.n)
     return {"workload": "batch4096", "systems": b.S, "terms": b.T, "precision": "dd",
             "ms_per_step": step_ms, "system_steps_per_s": b.S / (step_ms / 1e3), "all_ok": ok,
-            "loop_plain_ms_per_step_est": loop_total_ms,
-            "loop_plain_sample": f"{loop_sample} systems spread over the sizes, mean x {b.S}",
+            "loop_plain_ms_per_step": loop_total_ms,
+            "loop_plain": f"one gn_newton step on each of the {b.S} systems in turn, measured "
+                          f"(best of 2 loops; loading the systems and capturing their steps, "
+                          f"{load_s:.0f} s, untimed)",
             "speedup_vs_loop": loop_total_ms / step_ms,
             "mgs_imad_per_step": imad,
             "mgs_imad_rate_lower_bound": {"achieved": imad / (step_ms / 1e3) / 1e9, "unit": "G IMAD/s",
-                                          "peak": IMAD_PEAK_GINSTR,
-                                          "frac": imad / (step_ms / 1e3) / 1e9 / IMAD_PEAK_GINSTR,
+                                          "peak": peaks["imad_ginstr"],
+                                          "frac": imad / (step_ms / 1e3) / 1e9 / peaks["imad_ginstr"],
                                           "note": "MGS work only over the whole step time (evaluation not counted)"},
             "generate_s": gen_s}
 
 
-def breakdown(S, system, dev, flush, args):
+def eval_bytes(system, L):
+    """Algorithmic DRAM bytes of one evaluation in this library's layout: the
+    packed occurrences (4 B: variable and exponent), term offsets (4 B), the
+    coefficients (16 L B per term), x, f and the dense J (16 L B per entry)."""
+    W = 16 * L
+    return (4 * system.nnz + 4 * (system.T + 1) + W * system.T
+            + W * (system.n + system.N + system.N * system.n))
+
+
+def breakdown(S, system, dev, flush, args, peaks, rates):
     """Per-precision eval+diff (integer and FP64 arithmetic), least-squares and
     step times, and the roofline of the factorisation kernel (device events,
     L2 flushed before every timed call)."""
@@ -732,8 +860,22 @@ def breakdown(S, system, dev, flush, args):
         S.set_arith("auto")
         g = ev_ops / (ev["fp64"]["ms"] / 1e3) / 1e9
         ev["fp64"]["fp64_ginstr_per_s"] = g
-        ev["fp64"]["frac_of_fp64_peak"] = g / FP64_PEAK_GINSTR
+        ev["fp64"]["frac_of_fp64_peak"] = g / peaks["fp64_ginstr"]
+        fm = rates.get("fp64_fma", {}).get("rate")
+        ev["fp64"]["frac_of_fp64_measured"] = g / fm if fm else None
         ev["int"]["speedup_vs_fp64"] = ev["fp64"]["ms"] / ev["int"]["ms"]
+        if L == 1:
+            # double: the binding roofline is the larger of the HBM time of the
+            # algorithmic bytes and the FP64 time of the algorithmic
+            # instructions (L2 flushed before each timed call)
+            by = eval_bytes(system, L)
+            t = ev["fp64"]["ms"] / 1e3
+            t_hbm = by / (peaks["hbm_gbs"] * 1e9)
+            t_fp = ev_ops / (peaks["fp64_ginstr"] * 1e9)
+            ev["fp64"]["binding_roofline"] = {
+                "bound": "hbm" if t_hbm >= t_fp else "fp64", "frac": max(t_hbm, t_fp) / t,
+                "algorithmic_bytes": by, "achieved_gbs": by / t / 1e9, "hbm_peak_gbs": peaks["hbm_gbs"],
+                "fp64_frac": t_fp / t, "hbm_frac": t_hbm / t}
         out["eval_diff"][prec] = ev
         S.eval(prec, x, f, J)
         Ab0 = torch.cat([J, -f[None]], 0).contiguous()
@@ -752,10 +894,12 @@ def breakdown(S, system, dev, flush, args):
             assert int(status.item()) == 0
             work = algorithmic_imad_mgs(system.N, system.n + 1, L)
             achieved = work / (t_mgs / 1e3) / 1e9
+            mi = rates.get("imad", {}).get("rate")
             roof = {"kernel": f"k_mgs_int<{L}> (MGS on [J, -f], {system.N} x {system.n + 1})",
-                    "bound": "alu", "achieved": achieved, "peak": IMAD_PEAK_GINSTR,
-                    "unit": "G IMAD/s", "frac": achieved / IMAD_PEAK_GINSTR,
-                    "peak_source": "derived: 64 IMAD lanes/clk/SM x 152 SMs x 2.07 GHz",
+                    "bound": "alu", "achieved": achieved, "peak": peaks["imad_ginstr"],
+                    "unit": "G IMAD/s", "frac": achieved / peaks["imad_ginstr"],
+                    "peak_source": "derived: " + peaks["derivation"],
+                    "frac_of_measured_imad": achieved / mi if mi else None,
                     "traffic": MGS_TRAFFIC.get(L),
                     "traffic_source": "dram__bytes_read.sum + dram__bytes_write.sum per launch",
                     "algorithmic_imad": work, "launch_ms": t_mgs,

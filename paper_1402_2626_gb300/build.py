@@ -18,6 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgn.so")
+# the pipe issue-rate probes bench.py reports (not part of the Gauss-Newton path)
+PROBE_SRC = os.path.join(HERE, "probe", "rates.cu")
+PROBE_LIB = os.path.join(HERE, "librates.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", *ARCH]
 
@@ -39,10 +42,10 @@ def _deps():
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PROBE_LIB):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
+    return all(os.path.getmtime(d) <= t for d in _deps() + [PROBE_SRC])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -59,6 +62,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    probe_tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    procs.append((PROBE_SRC, subprocess.Popen([cc, *NVCC_FLAGS, "-shared", PROBE_SRC, "-o", probe_tmp],
+                                              stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -72,6 +78,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.run([cc, "-shared", *ARCH, "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    os.replace(probe_tmp, PROBE_LIB)
     return LIB
 
 
