@@ -355,12 +355,84 @@ def run_section(args):
     torch.cuda.set_device(dev)
     build.build()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
-    fn = {"adjoint": lambda: adjoint_extra(dev, flush, args),
+    fn = {"eval": lambda: eval_section(dev, flush, args),
+          "mgs": lambda: mgs_section(dev, flush, args),
+          "adjoint": lambda: adjoint_extra(dev, flush, args),
           "mixed": lambda: mixed_extra(dev, flush, args),
           "paper": lambda: paper_extra(dev, flush, args),
           "batched": lambda: batched(dev, args, device_peaks(dev))}[args.only]
     print(json.dumps({"section": args.only, args.only: fn()}), flush=True)
     return 0
+
+
+def _timed_calls(fn, stream, flush, reps, prep=None):
+    """Median device time (ms) of ``fn`` over ``reps`` calls, L2 flushed and
+    ``prep`` run before each (outside the events), after one untimed call."""
+    import torch
+
+    if prep:
+        prep()
+    fn()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        if prep:
+            prep()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def eval_section(dev, flush, args):
+    """Evaluation and differentiation of the gn256 workload (gn_eval, f and
+    the dense J, default arithmetic) at the precision of --prec, alone: for
+    one-kernel profiles of the evaluation kernels."""
+    import torch
+
+    from paper_1402_2626_gb300 import gn
+
+    L = PRECS[args.prec]
+    system = rank_system(0)
+    S = gn.System(system)
+    x = torch.tensor(system.point("x0", L), device=dev)
+    f = torch.empty((system.N, 2, L), dtype=torch.float64, device=dev)
+    J = torch.empty((system.n, system.N, 2, L), dtype=torch.float64, device=dev)
+    ms = _timed_calls(lambda: S.eval(args.prec, x, f, J), torch.cuda.current_stream(dev), flush,
+                      max(3, min(args.steps, 5)))
+    S.close()
+    return {"workload": WORKLOAD, "precision": args.prec, "ms": ms,
+            "monomials_per_s": system.T / (ms / 1e3), "algorithmic_bytes": eval_bytes(system, L)}
+
+
+def mgs_section(dev, flush, args):
+    """The factorisation alone (gn_mgs: k_mgs_int on the 256 x 257 matrix
+    [J, -f] of the gn256 workload at x0) at the precision of --prec: for
+    one-kernel profiles of the MGS kernel."""
+    import torch
+
+    from paper_1402_2626_gb300 import gn
+
+    L = PRECS[args.prec]
+    system = rank_system(0)
+    S = gn.System(system)
+    x = torch.tensor(system.point("x0", L), device=dev)
+    f = torch.empty((system.N, 2, L), dtype=torch.float64, device=dev)
+    J = torch.empty((system.n, system.N, 2, L), dtype=torch.float64, device=dev)
+    S.eval(args.prec, x, f, J)
+    Ab0 = torch.cat([J, -f[None]], 0).contiguous()
+    Ab = Ab0.clone()
+    R = torch.empty((system.n + 1, system.n + 1, 2, L), dtype=torch.float64, device=dev)
+    status = torch.zeros((1,), dtype=torch.int32, device=dev)
+    ms = _timed_calls(lambda: S.mgs(args.prec, Ab, R, status), torch.cuda.current_stream(dev),
+                      flush, max(3, min(args.steps, 5)), prep=lambda: Ab.copy_(Ab0))
+    ok = int(status.item()) == 0
+    S.close()
+    return {"workload": WORKLOAD, "precision": args.prec, "ms": ms, "status_ok": ok,
+            "algorithmic_imad": algorithmic_imad_mgs(system.N, system.n + 1, L)}
 
 
 def run_reference(args):
@@ -405,7 +477,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip per-precision breakdowns")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
-    ap.add_argument("--only", choices=["adjoint", "mixed", "paper", "batched"],
+    ap.add_argument("--only", choices=["eval", "mgs", "adjoint", "mixed", "paper", "batched"],
                     help="run one extra section alone and print it as the JSON line (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
