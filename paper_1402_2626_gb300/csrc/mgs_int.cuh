@@ -29,8 +29,8 @@ __device__ __forceinline__ uint32_t cl_mapa(uint32_t a, uint32_t r) {
   return d;
 }
 
-__device__ __forceinline__ void mb_init(uint64_t *bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+__device__ __forceinline__ void mb_init(uint64_t *bar, uint32_t count = 1) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
 // this CTA's arrival for the current phase, announcing `bytes` to come
@@ -90,6 +90,15 @@ __device__ __forceinline__ void mb_arrive(uint64_t *bar) {
 constexpr int MF_CW = MF_WARPS - 1;
 constexpr int MF_CT = MF_CW * 32;
 constexpr int MF_NPUB = 4;  // pivots handed to the publisher warp in flight
+// The pivot chain (the column after the current pivot: its dot with q_k,
+// axpy, norm, reciprocal square root and normalisation) runs on MF_QW warps
+// of each CTA; in each, lane 4 d + p takes rows 8 w + d (+32 i) and one of
+// the four real products of each complex one, so a lane's dependent chain
+// is a quarter of a whole complex product.  Integer sums are exact, so the
+// results are those of one warp doing all four products.
+constexpr int MF_QW = 4;
+constexpr int MF_QS = MF_QW * 8;  // reduction slots of one chain sum: a warp per CTA, 8 CTAs
+static_assert(MF_QS <= 32, "a chain sum is read by one lane per slot");
 
 __device__ __forceinline__ void cw_sync() { asm volatile("bar.sync 1, %0;" ::"n"(MF_CT) : "memory"); }
 
@@ -150,10 +159,36 @@ __device__ void warp_cluster_sum(fx<N> (&v)[NV], const MbSite &site, uint32_t u,
   }
 }
 
+// Exact cluster-wide sum as warp_cluster_sum, sent by MF_QW warps of every
+// CTA (the chain warps; cs is the caller's index among them): each sends its
+// warp total to slot [cs][rank] of every CTA, and every calling warp adds
+// all MF_QS slots, one lane per slot.  Chain warp 0 announces the bytes.
+template <int N>
+__device__ void chain_cluster_sum(fx<N> &v, const MbSite &site, uint32_t u, int rank, int cs,
+                                  int32_t *status) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t b = u & 1, par = (u >> 1) & 1;
+  uint64_t *bar = site.bar + b;
+  uint64_t *sl = site.slot + (size_t)b * MF_QS * N;
+  if (cs == 0 && lane == 0) mb_expect(bar, MF_QS * N * 8);
+  v = warp_sum_fx<N>(v);
+  if (lane < MF_C) {
+    const uint32_t ra = cl_mapa(smem_u32(sl + (size_t)(cs * MF_C + rank) * N), lane);
+    const uint32_t rb = cl_mapa(smem_u32(bar), lane);
+#pragma unroll
+    for (int w = 0; w < N; w++) st_async8(ra + 8 * w, v.w[w], rb);
+  }
+  mb_wait(bar, par, status);
+#pragma unroll
+  for (int w = 0; w < N; w++) v.w[w] = (lane < MF_QS) ? sl[(size_t)lane * N + w] : 0;
+  v = warp_sum_fx<N>(v);
+}
+
 // Columns per ownership block: column j belongs to cluster (j / MF_B) mod G,
 // so the pivot chain stays inside one cluster for MF_B - 1 of every MF_B
 // columns.
 constexpr int MF_B = 4;
+static_assert(MF_B + MF_QW - 1 <= MF_CW, "chain warps: the pivot's own warp and warps MF_B ..");
 
 // shared-memory layout of k_mgs_int, identical on host and device
 template <int L>
@@ -161,8 +196,8 @@ struct MiLayout {
   static constexpr int K = L;
   static constexpr int SW_PIV = 2 * K + 1;  // norm: 2K+1 limbs
   static constexpr int SW_DOT = 2 * (K + 1);  // a dot: re, im of K+1 limbs
-  static constexpr int NBAR = 6 + 2 * MF_NPUB;  // 3 sites x 2, publication full/empty
-  size_t oS, oTb, oN0, oN0p, oR, oQ, oBar, oPub, oPiv, oLa, oBulk, oA, bytes;
+  static constexpr int NBAR = 8 + 2 * MF_NPUB;  // 4 sites x 2, publication full/empty
+  size_t oS, oTb, oN0, oN0p, oR, oQ, oBar, oPub, oPiv, oCh, oLa, oBulk, oA, bytes;
   __host__ __device__ MiLayout(int maxown, int ms, bool cols) {
     size_t o = 0;
     auto take = [&](size_t b) {
@@ -179,8 +214,9 @@ struct MiLayout {
     oQ = take(sizeof(fx<K>) * 2 * msr);                // a pivot slice read from global memory
     oBar = take(sizeof(uint64_t) * NBAR);              // mbarriers
     oPub = take(sizeof(int) * 2 * MF_NPUB);            // handed-off pivots: column, accepted
-    oPiv = take(sizeof(uint64_t) * 2 * MF_C * SW_PIV);
-    oLa = take(sizeof(uint64_t) * 2 * MF_B * MF_C * SW_DOT);
+    oPiv = take(sizeof(uint64_t) * 2 * MF_QS * SW_PIV);
+    oCh = take(sizeof(uint64_t) * 2 * MF_QS * SW_DOT);
+    oLa = take(sizeof(uint64_t) * 2 * (MF_B - 1) * MF_C * SW_DOT);
     oBulk = take(sizeof(uint64_t) * 2 * (size_t)maxown * MF_C * SW_DOT);
     oA = take(cols ? sizeof(fx<K>) * 2 * msr * maxown : 0);  // the CTA's rows of its columns
     bytes = (o + 255) & ~(size_t)255;
@@ -229,15 +265,17 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   fx<K> *sQ = (fx<K> *)(smem + lay.oQ);  // [ms][2]
   fx<K> *sA = (fx<K> *)(smem + lay.oA);  // [maxown][ms][2]
   uint64_t *bars = (uint64_t *)(smem + lay.oBar);
-  uint64_t *pubFull = bars + 6, *pubEmpty = bars + 6 + MF_NPUB;
+  uint64_t *pubFull = bars + 8, *pubEmpty = bars + 8 + MF_NPUB;
   int *sPubJ = (int *)(smem + lay.oPub), *sPubAcc = sPubJ + MF_NPUB;
   MbSite piv{bars + 0, (uint64_t *)(smem + lay.oPiv), 0};
-  MbSite la{bars + 2, (uint64_t *)(smem + lay.oLa), 0};
+  MbSite la{bars + 2, (uint64_t *)(smem + lay.oLa), 0};  // the block's later columns
   MbSite bulk{bars + 4, (uint64_t *)(smem + lay.oBulk), 0};
+  MbSite ch{bars + 6, (uint64_t *)(smem + lay.oCh), 0};  // the chain column's dot
   bool ok = true;
 
   if (tid == 0) {
-    for (int q = 0; q < MiLayout<L>::NBAR; q++) mb_init(bars + q);
+    for (int q = 0; q < MiLayout<L>::NBAR; q++)
+      mb_init(bars + q, (q >= 8 && q < 8 + MF_NPUB) ? MF_QW : 1);  // pubFull: every chain warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
 
@@ -300,32 +338,36 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
   }
   __syncthreads();
 
-  // Pivot j by the one warp of each CTA that owns local column lcol(j): exact
-  // norm, cluster sum, 1/||a_j|| by integer Newton in lane 0, rank test,
-  // normalisation (into the CTA's column and the publication slot),
-  // release of the flag; the R diagonal and 1/r_jj afterwards.
-  auto pivot = [&](int j, uint32_t u) {
+  // the chain warps: lane 4 d + p of chain warp cs takes rows 8 cs + d
+  // (+32 i) and the part p of each (rows of a warp-uniform block rb)
+  const int qp = lane & 3, qd = lane >> 2;
+
+  // Pivot j by the MF_QW chain warps of each CTA (cs = index among them):
+  // exact norm (squares of the real parts in lanes p = 0, of the imaginary
+  // parts in p = 1), cluster sum, 1/||a_j|| by integer Newton in lane 0 of
+  // every chain warp (the same value in each), rank test, normalisation of
+  // the warp's rows (into the CTA's column and the publication slot), hand-
+  // off to the publisher; the R diagonal and 1/r_jj afterwards.
+  auto pivot = [&](int j, uint32_t u, int cs) {
     const int c = lcol(j);
     fx<K> *aj = colp(c);
     const int sj = sS[c];
-    fx<2 * K + 1> t[1];
-    fx_zero<2 * K + 1>(t[0]);
-    for (int r = lane; r < nr; r += 32) {
-      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * r]));
-      t[0] = ix_add<2 * K + 1>(t[0], ix_square<K>(aj[2 * r + 1]));
-    }
-    warp_cluster_sum<2 * K + 1, 1>(t, piv, u, rank, a.status);
+    fx<2 * K + 1> t;
+    fx_zero<2 * K + 1>(t);
+    for (int r = 8 * cs + qd; r < nr; r += 32)
+      if (qp < 2) t = ix_add<2 * K + 1>(t, ix_square<K>(aj[2 * r + qp]));
+    chain_cluster_sum<2 * K + 1>(t, piv, u, rank, cs, a.status);
     ux<K> Y;
     fx<K> Z;
     ux<K> tt;
     int bl = 0, b = 0, accept = 0;
     fx_zero<K>(Z);
     if (lane == 0) {
-      const fx<2 * K + 1> T = t[0];
+      const fx<2 * K + 1> T = t;
       bl = ix_bitlen<2 * K + 1>(T);
       b = (bl + 1) >> 1;  // sqrt(T) < 2^b
       accept = (bl > 0) && (j == ncols - 1 || bl > sTb[c]);
-      if (!accept && j < ncols - 1) atomicCAS(a.status, GN_OK, GN_ESINGULAR);
+      if (!accept && j < ncols - 1 && cs == 0) atomicCAS(a.status, GN_OK, GN_ESINGULAR);
       // t = T / 2^(2b) in [1/4, 1) as K limbs of fraction
       {
         fx<2 * K + 1> sh;
@@ -355,7 +397,9 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
         uint64_t nz;
         const ux<K> uz = ix_abs<K>(Z, nz);
         fx<K> *pj = pubp(j);
-        for (int e = lane; e < 2 * nr; e += 32) {
+        for (int r = 8 * cs + qd; r < nr; r += 32) {
+          if (qp >= 2) continue;
+          const int e = 2 * r + qp;
           uint64_t na;
           ux<K> ua = ix_abs<K>(aj[e], na);
           ux<2 * K> p = ix_umul<K>(ua, uz);
@@ -371,21 +415,24 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
           if (a.smem_cols) pj[e] = q;
         }
       }
-      // hand q_j to the publisher warp: the warp's stores are ordered before
-      // lane 0's arrival (release), the publisher's flag release after it
+      // hand q_j to the publisher warp once every chain warp's rows are in:
+      // each warp's stores are ordered before its lane 0's arrival (release),
+      // the publisher's flag release after the last of them
       __syncwarp();
       if (lane == 0) {
         const int pp = lcol(j), ps = pp % MF_NPUB;
         if (mb_wait(pubEmpty + ps, ((pp / MF_NPUB) & 1) ^ 1, a.status)) {
-          sPubJ[ps] = j;
-          sPubAcc[ps] = accept;
+          if (cs == 0) {
+            sPubJ[ps] = j;
+            sPubAcc[ps] = accept;
+          }
           mb_arrive(pubFull + ps);
         }
       }
     }
     // for back substitution and the R output: 1/r_jj = Z 2^e, and t and b in
     // the diagonal slot of R (k_mgs_r_out forms r_jj and 1/r_jj from them)
-    if (lane == 0 && rank == 0) {
+    if (lane == 0 && rank == 0 && cs == 0) {
       if (accept && j < ncols - 1) {
         double *zs = a.Zs + (size_t)j * (K + 1);
 #pragma unroll
@@ -396,6 +443,51 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
 #pragma unroll
       for (int w = 0; w < K; w++) rd[w] = (bl > 0) ? tt.w[w] : 0;
       rd[K] = (uint64_t)b;
+    }
+  };
+
+  // the chain warps' share of conj(q)^T a over this CTA's rows for one
+  // column: lanes p = 0, 1 add qr ar, qi ai (real part), p = 2, 3 add
+  // qr ai, -qi ar (imaginary part); each part summed over the warp
+  auto chain_dot = [&](const fx<K> *q, const fx<K> *aj, int cs, fx<K + 1> &dr, fx<K + 1> &di) {
+    const int qo = (qp == 1 || qp == 3) ? 1 : 0, ao = (qp == 1 || qp == 2) ? 1 : 0;
+    fx<K + 1> acc;
+    fx_zero<K + 1>(acc);
+    for (int r = 8 * cs + qd; r < nr; r += 32)
+      acc = ix_add_cneg<K + 1>(acc, ix_mul_shift<K>(q[2 * r + qo], aj[2 * r + ao]), qp == 3);
+    fx<K + 1> pr, pi;
+#pragma unroll
+    for (int w = 0; w <= K; w++) {
+      pr.w[w] = qp < 2 ? acc.w[w] : 0;
+      pi.w[w] = qp < 2 ? 0 : acc.w[w];
+    }
+    dr = warp_sum_fx<K + 1>(pr);
+    di = warp_sum_fx<K + 1>(pi);
+  };
+
+  // the chain warps' rows of a_j <- a_j - r q: lane p forms rr qr, ri qi,
+  // rr qi, ri qr (p = 0 .. 3); lane 0 of a quad takes the real part
+  // rr qr - ri qi, lane 2 the imaginary part rr qi + ri qr, from its
+  // partner's product (the same integer results as one lane forming all four)
+  auto chain_axpy = [&](const fx<K> *q, fx<K> *aj, int cs, const fx<K> &rr, const fx<K> &ri) {
+    const int qo = (qp == 1 || qp == 2) ? 1 : 0;
+    const fx<K> rv = (qp & 1) ? ri : rr;
+    for (int rb = 8 * cs; rb < nr; rb += 32) {  // warp-uniform: every lane shuffles
+      const int r = rb + qd;
+      fx<K + 1> pr;
+      if (r < nr) {
+        pr = ix_mul_shift<K>(rv, q[2 * r + qo]);
+      } else {
+        fx_zero<K + 1>(pr);
+      }
+      fx<K + 1> po;
+#pragma unroll
+      for (int w = 0; w <= K; w++) po.w[w] = __shfl_xor_sync(0xffffffffu, pr.w[w], 1);
+      if (r < nr && (qp & 1) == 0) {
+        const fx<K + 1> d = ix_add_cneg<K + 1>(pr, po, qp == 0);
+        fx<K> *x = aj + 2 * r + (qp >> 1);
+        *x = ix_narrow<K>(ix_sub<K + 1>(ix_widen<K, K + 1>(*x), d));
+      }
     }
   };
 
@@ -438,10 +530,10 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     }
   };
 
-  // send this warp's dot to slot [t][rank] of every CTA of the cluster
-  auto send_dot = [&](uint64_t *sl, uint64_t *bar, int t, const fx<K + 1> &dr, const fx<K + 1> &di) {
+  // send this warp's dot to slot [base + rank] of every CTA of the cluster
+  auto send_dot = [&](uint64_t *sl, uint64_t *bar, int base, const fx<K + 1> &dr, const fx<K + 1> &di) {
     if (lane < MF_C) {
-      const uint32_t ra = cl_mapa(smem_u32(sl + ((size_t)t * MF_C + rank) * SWD), lane);
+      const uint32_t ra = cl_mapa(smem_u32(sl + ((size_t)base + rank) * SWD), lane);
       const uint32_t rb = cl_mapa(smem_u32(bar), lane);
 #pragma unroll
       for (int w = 0; w < K + 1; w++) {
@@ -451,20 +543,72 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
     }
   };
 
-  // Apply q_k (this CTA's rows at q) to the local columns [cf, no): dots by
-  // warps, totals through the bulk site, axpys.  Every thread calls it.
-  auto bulk_apply = [&](int k, const fx<K> *q, int cf) {
-    const int nb = no - cf;
+  // conj(q)^T a for two columns at once, by one warp (two independent
+  // product chains per lane; q's rows are loaded once)
+  auto warp_dot2 = [&](const fx<K> *q, const fx<K> *a1, const fx<K> *a2, fx<K + 1> (&d)[4]) {
+#pragma unroll
+    for (int v = 0; v < 4; v++) fx_zero<K + 1>(d[v]);
+    for (int r = lane; r < nr; r += 32) {
+      const fx<K> qr = q[2 * r], qi = q[2 * r + 1];
+      const fx<K> ar = a1[2 * r], ai = a1[2 * r + 1], br = a2[2 * r], bi = a2[2 * r + 1];
+      d[0] = ix_add<K + 1>(d[0], ix_mul_shift<K>(qr, ar));
+      d[2] = ix_add<K + 1>(d[2], ix_mul_shift<K>(qr, br));
+      d[0] = ix_add<K + 1>(d[0], ix_mul_shift<K>(qi, ai));
+      d[2] = ix_add<K + 1>(d[2], ix_mul_shift<K>(qi, bi));
+      d[1] = ix_add<K + 1>(d[1], ix_mul_shift<K>(qr, ai));
+      d[3] = ix_add<K + 1>(d[3], ix_mul_shift<K>(qr, bi));
+      d[1] = ix_sub<K + 1>(d[1], ix_mul_shift<K>(qi, ar));
+      d[3] = ix_sub<K + 1>(d[3], ix_mul_shift<K>(qi, br));
+    }
+#pragma unroll
+    for (int v = 0; v < 4; v++) d[v] = warp_sum_fx<K + 1>(d[v]);
+  };
+
+  // a1 <- a1 - r1 q and a2 <- a2 - r2 q over this CTA's rows, by one warp
+  auto warp_axpy2 = [&](const fx<K> *q, fx<K> *a1, fx<K> *a2, const fx<K> &r1r, const fx<K> &r1i,
+                        const fx<K> &r2r, const fx<K> &r2i) {
+    for (int r = lane; r < nr; r += 32) {
+      const fx<K> qr = q[2 * r], qi = q[2 * r + 1];
+      fx<K + 1> xr = ix_widen<K, K + 1>(a1[2 * r]), xi = ix_widen<K, K + 1>(a1[2 * r + 1]);
+      fx<K + 1> yr = ix_widen<K, K + 1>(a2[2 * r]), yi = ix_widen<K, K + 1>(a2[2 * r + 1]);
+      xr = ix_sub<K + 1>(xr, ix_mul_shift<K>(r1r, qr));
+      yr = ix_sub<K + 1>(yr, ix_mul_shift<K>(r2r, qr));
+      xr = ix_add<K + 1>(xr, ix_mul_shift<K>(r1i, qi));
+      yr = ix_add<K + 1>(yr, ix_mul_shift<K>(r2i, qi));
+      xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(r1r, qi));
+      yi = ix_sub<K + 1>(yi, ix_mul_shift<K>(r2r, qi));
+      xi = ix_sub<K + 1>(xi, ix_mul_shift<K>(r1i, qr));
+      yi = ix_sub<K + 1>(yi, ix_mul_shift<K>(r2i, qr));
+      a1[2 * r] = ix_narrow<K>(xr);
+      a1[2 * r + 1] = ix_narrow<K>(xi);
+      a2[2 * r] = ix_narrow<K>(yr);
+      a2[2 * r + 1] = ix_narrow<K>(yi);
+    }
+  };
+
+  // Apply q_k (this CTA's rows at q) to the local columns [c0, c1): dots by
+  // warps (column c0 + cc on warp cc mod MF_CW, two of a warp's columns at a
+  // time), totals through the bulk site, axpys.  Every thread calls it.
+  auto bulk_apply = [&](int k, const fx<K> *q, int c0, int c1) {
+    const int nb = c1 - c0;
     if (nb <= 0) return;
     const uint32_t u = bulk.use++;
     const uint32_t bb = u & 1, par = (u >> 1) & 1;
     uint64_t *bar = bulk.bar + bb;
     uint64_t *sl = bulk.slot + (size_t)bb * a.maxown * MF_C * SWD;
     if (tid == 0) mb_expect(bar, (uint32_t)(nb * MF_C * SWD * 8));
-    for (int cc = warp; cc < nb; cc += MF_CW) {
-      fx<K + 1> dr, di;
-      warp_dot(q, colp(cf + cc), dr, di);
-      send_dot(sl, bar, cc, dr, di);
+    for (int cc = warp; cc < nb; cc += 2 * MF_CW) {
+      const int c2 = cc + MF_CW;
+      if (c2 < nb) {
+        fx<K + 1> d[4];
+        warp_dot2(q, colp(c0 + cc), colp(c0 + c2), d);
+        send_dot(sl, bar, cc * MF_C, d[0], d[1]);
+        send_dot(sl, bar, c2 * MF_C, d[2], d[3]);
+      } else {
+        fx<K + 1> dr, di;
+        warp_dot(q, colp(c0 + cc), dr, di);
+        send_dot(sl, bar, cc * MF_C, dr, di);
+      }
     }
     mb_wait(bar, par, a.status);
     for (int cc = tid; cc < nb; cc += MF_CT) {
@@ -484,10 +628,18 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       }
       sR[2 * cc] = ix_narrow<K>(tr);
       sR[2 * cc + 1] = ix_narrow<K>(ti);
-      if (rank == 0) out_r(k, cf + cc, tr, ti);
+      if (rank == 0) out_r(k, c0 + cc, tr, ti);
     }
     cw_sync();
-    for (int cc = warp; cc < nb; cc += MF_CW) warp_axpy(q, colp(cf + cc), sR[2 * cc], sR[2 * cc + 1]);
+    for (int cc = warp; cc < nb; cc += 2 * MF_CW) {
+      const int c2 = cc + MF_CW;
+      if (c2 < nb) {
+        warp_axpy2(q, colp(c0 + cc), colp(c0 + c2), sR[2 * cc], sR[2 * cc + 1], sR[2 * c2],
+                   sR[2 * c2 + 1]);
+      } else {
+        warp_axpy(q, colp(c0 + cc), sR[2 * cc], sR[2 * cc + 1]);
+      }
+    }
     cw_sync();  // sR, sQ and the slots are free for the next use
   };
 
@@ -517,30 +669,64 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       __syncwarp();
     }
   } else {
+  // the chain warps for pivot column j: warp (j mod B) and warps B ..
+  // B + MF_QW - 2, which the block's other columns leave free
+  auto chain_slot = [&](int j) {
+    return warp == (j & (B - 1)) ? 0 : ((warp >= B && warp < B + MF_QW - 1) ? warp - B + 1 : -1);
+  };
+
   if (owner(0) == g && no > 0) {
     const uint32_t u = piv.use++;
-    if (warp == 0) pivot(0, u);
+    const int cs = chain_slot(0);
+    if (cs >= 0) pivot(0, u, cs);
     cw_sync();
   }
 
-  int kp = 0;  // first q not yet applied to the columns outside the current block
-  int cf = 0;  // first local column with global index > k
+  // Progress of the bulk updates, in MGS order per column: the columns of
+  // the cluster's next block (local [cf, cf + B), which lead the chain when
+  // it reaches the cluster) have received the q's before kn, the cluster's
+  // later columns those before kp.  While the chain is within one step of the
+  // next block, only that block is updated (the later columns wait until the
+  // chain has left the cluster); otherwise every later column is.
+  int kp = 0, kn = 0;
+  int cfb = -1;  // the block kn refers to (its first local column)
+  int cf = 0;    // first local column with global index > k
   for (int k = 0; k < ncols - 1; k++) {
     if (k >= jlast) break;
     while (cf < no && gcol(cf) <= k) cf++;
+    if (cf != cfb) {  // a new next block: its columns are where the later ones are
+      kn = kp;
+      cfb = cf;
+    }
     const bool lak = owner(k + 1) == g;  // this cluster takes the pivot chain
-    // columns outside the block get the pending q's first (MGS order), also
-    // before a new block of this cluster starts
-    if (!lak || (k + 1) % B == 0) {
-      for (int kk = kp; kk < k; kk++) {
+    const int cb = min(cf + B, no);
+    // the chain reaches this cluster's next block right after q_{k+1}
+    const bool near = !lak && k + 2 < ncols && owner(k + 2) == g;
+    // this iteration's bulk updates: column ranges [rc0, rc1) with the first
+    // q each still lacks (rk); one range when the next block and the later
+    // columns are level, else the block first
+    int rk[2], rc0[2], rc1[2], nrg = 0;
+    if (!lak) {
+      if (kn == kp && !near) {
+        rk[0] = kp, rc0[0] = cf, rc1[0] = no, nrg = 1;
+      } else {
+        rk[0] = kn, rc0[0] = cf, rc1[0] = cb, nrg = 1;
+        if (!near) rk[1] = kp, rc0[1] = cb, rc1[1] = no, nrg = 2;
+      }
+    } else if ((k + 1) % B == 0) {  // a new block of this cluster takes the chain at k+1
+      rk[0] = kn, rc0[0] = cf, rc1[0] = cb, nrg = 1;
+    }
+    // the q's before q_k that the ranges lack
+    for (int r = 0; r < nrg; r++) {
+      for (int kk = rk[r]; kk < k; kk++) {
+        const fx<K> *qq = sQ;
         if (owner(kk) == g) {
-          bulk_apply(kk, colp(lcol(kk)), cf);
+          qq = colp(lcol(kk));
         } else {
           load_q(kk);
-          bulk_apply(kk, sQ, cf);
         }
+        bulk_apply(kk, qq, rc0[r], rc1[r]);
       }
-      kp = k;
     }
     // q_k: this cluster's own, or published by its owner
     const fx<K> *q;
@@ -576,44 +762,65 @@ __global__ void __launch_bounds__(MF_THREADS, 1) k_mgs_int(MfArgs a) {
       q = sQ;
     }
     if (lak) {
-      // the block's columns after k, warp (j mod B) each: dot, cluster sum, axpy;
-      // then the pivot k+1 by its warp, which publishes q_{k+1}
+      // the block's columns after k: column k+1 (the chain) on the MF_QW chain
+      // warps, each later one on warp (j mod B): dot, cluster sum, axpy; then
+      // the pivot k+1 on the chain warps, which publishes q_{k+1}.  Slots of
+      // column j1 + t start at t MF_QS; the chain's fill MF_QS of them, the
+      // others MF_C.
       const int j1 = k + 1, jend = min(((k + 1) / B + 1) * B, ncols), nla = jend - j1;
-      const uint32_t u = la.use++;
-      const uint32_t bb = u & 1, par = (u >> 1) & 1;
-      uint64_t *bar = la.bar + bb;
-      uint64_t *sl = la.slot + (size_t)bb * B * MF_C * SWD;
-      if (tid == 0) mb_expect(bar, (uint32_t)(nla * MF_C * SWD * 8));
-      const int t = warp - (j1 % B);  // this warp's column j1 + t
-      if (warp < B && t >= 0 && t < nla) {
+      // the chain column's dot on its own site (the chain does not wait for
+      // the later columns' dots); the later columns on the window site
+      const uint32_t uc = ch.use++;
+      const uint32_t uw = nla > 1 ? la.use++ : 0u;
+      const int cs = chain_slot(j1);
+      const int t = cs >= 0 ? 0 : warp - (j1 % B);  // this warp's column j1 + t
+      if (cs >= 0 || (warp < B && t > 0 && t < nla)) {
+        const uint32_t u = cs >= 0 ? uc : uw;
+        const uint32_t bb = u & 1, par = (u >> 1) & 1;
+        uint64_t *bar = (cs >= 0 ? ch.bar : la.bar) + bb;
+        uint64_t *sl = cs >= 0 ? ch.slot + (size_t)bb * MF_QS * SWD
+                               : la.slot + (size_t)bb * (B - 1) * MF_C * SWD;
+        const int base = cs >= 0 ? 0 : (t - 1) * MF_C;  // first slot of this column
+        if (lane == 0 && cs == 0) mb_expect(bar, (uint32_t)(MF_QS * SWD * 8));
+        if (lane == 0 && t == 1) mb_expect(bar, (uint32_t)((nla - 1) * MF_C * SWD * 8));
         const int c = lcol(j1 + t);
         fx<K> *aj = colp(c);
         fx<K + 1> dr, di;
-        warp_dot(q, aj, dr, di);
-        send_dot(sl, bar, t, dr, di);
+        if (cs >= 0) {
+          chain_dot(q, aj, cs, dr, di);
+        } else {
+          warp_dot(q, aj, dr, di);
+        }
+        send_dot(sl, bar, base + (cs > 0 ? cs : 0) * MF_C, dr, di);
         mb_wait(bar, par, a.status);
+        const int ns = cs >= 0 ? MF_QS : MF_C;
         fx<K + 1> v[2];
 #pragma unroll
         for (int w = 0; w < K + 1; w++) {
-          v[0].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + w] : 0;
-          v[1].w[w] = (lane < MF_C) ? sl[((size_t)t * MF_C + lane) * SWD + K + 1 + w] : 0;
+          v[0].w[w] = (lane < ns) ? sl[((size_t)base + lane) * SWD + w] : 0;
+          v[1].w[w] = (lane < ns) ? sl[((size_t)base + lane) * SWD + K + 1 + w] : 0;
         }
         v[0] = warp_sum_fx<K + 1>(v[0]);
         v[1] = warp_sum_fx<K + 1>(v[1]);
-        warp_axpy(q, aj, ix_narrow<K>(v[0]), ix_narrow<K>(v[1]));
-        if (t > 0 && lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
-        if (t == 0) {
+        if (cs >= 0) {
+          chain_axpy(q, aj, cs, ix_narrow<K>(v[0]), ix_narrow<K>(v[1]));
           const uint32_t pu = piv.use;
-          pivot(j1, pu);
+          pivot(j1, pu, cs);
+          if (cs == 0 && lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
+        } else {
+          warp_axpy(q, aj, ix_narrow<K>(v[0]), ix_narrow<K>(v[1]));
           if (lane == 0 && rank == 0) out_r(k, c, v[0], v[1]);
         }
       }
       piv.use++;
       cw_sync();  // q_{k+1} and the block's columns are visible to every compute warp
     } else {
-      bulk_apply(k, q, cf);
-      kp = k + 1;
+      // q_k to the ranges, which now lack nothing before it
+      for (int r = 0; r < nrg; r++) bulk_apply(k, q, rc0[r], rc1[r]);
+      kn = k + 1;
+      if (!near) kp = k + 1;
     }
+    if (lak && (k + 1) % B == 0) kn = k;
   }
   }  // compute warps
   __syncthreads();
