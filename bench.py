@@ -818,8 +818,9 @@ def batched(dev, args, peaks):
     x = x0.clone()
     status = torch.zeros((b.S,), dtype=torch.int32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    g.newton("dd", x, 1, status)  # tunes the solver's launch, captures the step
+    g.newton("dd", x, 1, status)  # tunes the launches, captures the step
     torch.cuda.synchronize()
+    tuning = g.tuning("dd")
     reps = max(3, min(args.steps, 10))
     ms = []
     for _ in range(reps):
@@ -864,6 +865,7 @@ def batched(dev, args, peaks):
     imad = sum(algorithmic_imad_mgs(int(n), int(n) + 1, L) for n in b.n)
     return {"workload": "batch4096", "systems": b.S, "terms": b.T, "precision": "dd",
             "ms_per_step": step_ms, "system_steps_per_s": b.S / (step_ms / 1e3), "all_ok": ok,
+            "tuning": tuning,
             "loop_plain_ms_per_step": loop_total_ms,
             "loop_plain": f"one gn_newton step on each of the {b.S} systems in turn, measured "
                           f"(best of 2 loops; loading the systems and capturing their steps, "

@@ -39,6 +39,8 @@ struct BatchWs {
   int32_t *zero = nullptr;     // status word the evaluation kernels read (always GN_OK)
   int32_t *counter = nullptr;  // [0] work queue position, [1] step index
   int threads = 0, grid = 0;   // tuned launch of the solver
+  int eval_block = 128;        // tuned CTA size of the per-term evaluation kernel
+  int sorted = 1;              // solver queue: largest systems first (1) or as stored (0)
   cudaGraphExec_t exec = nullptr;
   const double *gx = nullptr;
   double *gnorms = nullptr;
@@ -57,7 +59,7 @@ struct gn_batch {
   double *d_coef = nullptr;
   int32_t *d_jz_ptr = nullptr, *d_jz_occ = nullptr;
   int64_t *d_jz_out = nullptr, *d_f_out = nullptr;
-  int32_t *d_sys_n = nullptr, *d_order = nullptr;
+  int32_t *d_sys_n = nullptr, *d_order = nullptr, *d_order_id = nullptr;
   int64_t *d_x_off = nullptr, *d_A_off = nullptr, *d_R_off = nullptr, *d_C_off = nullptr;
   gn::BatchWs ws[5];
 };
@@ -425,6 +427,7 @@ static gn_status batch_eval(gn_batch *b, int L, BatchWs *w, const double *d_x, c
   a.f_out = b->d_f_out;
   a.neg_f = 1;
   a.status = w->zero;
+  a.block = w->eval_block;
   return launch_eval_int_raw(L, a, st);
 }
 
@@ -432,7 +435,7 @@ template <int L>
 static gn_status batch_solve_launch(gn_batch *b, BatchWs *w, double *d_x, double *norms, int32_t *status,
                                     int32_t max_steps, int threads, int grid, cudaStream_t st) {
   BsArgs a{w->A, w->Rm, w->Zs, d_x, b->d_A_off, b->d_R_off, b->d_C_off, b->d_x_off, b->d_sys_n,
-           b->d_order, b->S, w->counter, status, norms, max_steps};
+           w->sorted ? b->d_order : b->d_order_id, b->S, w->counter, status, norms, max_steps};
   k_batch_solve<L><<<grid, threads, 0, st>>>(a);
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
@@ -457,21 +460,63 @@ static int batch_occupancy(int threads) {
   return nb;
 }
 
-// Choose the solver's CTA size by timing one solve per candidate on a copy
-// of x (outside any capture).
+// The batch's autotuner (outside any capture, on a copy of x): first the CTA
+// size of the per-term evaluation kernel (64, 128 or 256 threads, one
+// monomial per thread; the kernel is instruction-bound and keeps its forward
+// products in local memory, so the CTA size moves occupancy and L1
+// residency), timed over every term of the batch; then the solver's launch
+// (CTA of 128 or 256 threads, grid = SMs x resident CTAs) and the order of
+// its work queue (largest systems first, or as stored), timed over one
+// solve of every system.  The fastest of each is kept.
 static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, cudaStream_t st) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return GN_ECUDA;
-  const int cand[2] = {128, 256};
   double *xs = nullptr;
   int32_t *stv = nullptr;
   gn_status e = bdalloc(&xs, 2 * (size_t)L * b->X);
   if (!e) e = bdalloc(&stv, (size_t)b->S);
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (!e && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) e = GN_ECUDA;
+  // x from the caller's copy, every system's status GN_OK, the queue at 0
+  auto reset = [&]() -> gn_status {
+    if (cudaMemcpyAsync(xs, d_x, sizeof(double) * 2 * L * b->X, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemsetAsync(stv, 0, sizeof(int32_t) * b->S, st) != cudaSuccess ||
+        cudaMemsetAsync(w->counter, 0, sizeof(int32_t) * 2, st) != cudaSuccess)
+      return GN_ECUDA;
+    return GN_OK;
+  };
+  auto elapsed = [&](float &ms) -> gn_status {
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      return GN_ECUDA;
+    return GN_OK;
+  };
+  // 1. the evaluation kernel's CTA size
+  const int ecand[3] = {64, 128, 256};
   float best = 1e30f;
+  int eb = 128;
+  for (int c = 0; c < 3 && !e; c++) {
+    w->eval_block = ecand[c];
+    e = reset();
+    if (!e) e = batch_eval(b, L, w, xs, st);  // warm-up
+    if (e) break;
+    cudaEventRecord(e0, st);
+    e = batch_eval(b, L, w, xs, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (!e) e = elapsed(ms);
+    if (!e && ms < best) {
+      best = ms;
+      eb = ecand[c];
+    }
+  }
+  w->eval_block = eb;
+  // 2. the solver's CTA size and queue order
+  const int cand[2] = {128, 256};
+  best = 1e30f;
+  w->threads = 0;
+  int keep_sorted = 1;
   for (int c = 0; c < 2 && !e; c++) {
     const int th = cand[c];
     if (th < std::min(b->max_n, 256)) continue;  // back substitution needs a thread per row
@@ -483,34 +528,31 @@ static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, c
     }
     if (occ <= 0) continue;
     const int grid = sms * occ;
-    if (cudaMemcpyAsync(xs, d_x, sizeof(double) * 2 * L * b->X, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
-        cudaMemsetAsync(stv, 0, sizeof(int32_t) * b->S, st) != cudaSuccess ||
-        cudaMemsetAsync(w->counter, 0, sizeof(int32_t) * 2, st) != cudaSuccess) {
-      e = GN_ECUDA;
-      break;
-    }
-    e = batch_eval(b, L, w, xs, st);
-    if (e) break;
-    cudaEventRecord(e0, st);
-    e = batch_solve(b, L, w, xs, nullptr, stv, 0, th, grid, st);
-    cudaEventRecord(e1, st);
-    if (e || cudaEventSynchronize(e1) != cudaSuccess) {
-      e = e ? e : GN_ECUDA;
-      break;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      w->threads = th;
-      w->grid = grid;
+    for (int sorted = 1; sorted >= 0 && !e; sorted--) {
+      w->sorted = sorted;
+      e = reset();
+      if (!e) e = batch_eval(b, L, w, xs, st);
+      if (e) break;
+      cudaEventRecord(e0, st);
+      e = batch_solve(b, L, w, xs, nullptr, stv, 0, th, grid, st);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (!e) e = elapsed(ms);
+      if (!e && ms < best) {
+        best = ms;
+        w->threads = th;
+        w->grid = grid;
+        keep_sorted = sorted;
+      }
     }
   }
+  w->sorted = keep_sorted;
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(xs);
   cudaFree(stv);
   if (!e && !w->threads) e = GN_ECUDA;
+  if (e) w->threads = 0;
   return e;
 }
 
@@ -694,6 +736,8 @@ gn_status gn_batch_create(gn_batch **out, int32_t S, const int64_t *h_sys_n, int
   if (!e) e = bupload(&b->d_f_out, f_out.data(), f_out.size());
   if (!e) e = bupload(&b->d_sys_n, sys_n.data(), sys_n.size());
   if (!e) e = bupload(&b->d_order, order.data(), order.size());
+  std::iota(order.begin(), order.end(), 0);  // the queue as stored
+  if (!e) e = bupload(&b->d_order_id, order.data(), order.size());
   if (!e) e = bupload(&b->d_x_off, x_off.data(), x_off.size());
   if (!e) e = bupload(&b->d_A_off, A_off.data(), A_off.size());
   if (!e) e = bupload(&b->d_R_off, R_off.data(), R_off.size());
@@ -720,6 +764,7 @@ gn_status gn_batch_destroy(gn_batch *b) {
   cudaFree(b->d_f_out);
   cudaFree(b->d_sys_n);
   cudaFree(b->d_order);
+  cudaFree(b->d_order_id);
   cudaFree(b->d_x_off);
   cudaFree(b->d_A_off);
   cudaFree(b->d_R_off);
@@ -736,6 +781,18 @@ gn_status gn_batch_info(const gn_batch *b, int32_t *S, int64_t *X, int64_t *T, i
   if (T) *T = b->T;
   if (nnz) *nnz = b->nnz;
   if (max_n) *max_n = b->max_n;
+  return GN_OK;
+}
+
+gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, int32_t *solve_threads,
+                          int32_t *solve_grid, int32_t *largest_first) {
+  if (!b || !(prec == 1 || prec == 2 || prec == 4)) return GN_EINVAL;
+  const BatchWs &w = b->ws[prec];
+  if (!w.threads) return GN_EINVAL;  // not tuned yet
+  if (eval_block) *eval_block = w.eval_block;
+  if (solve_threads) *solve_threads = w.threads;
+  if (solve_grid) *solve_grid = w.grid;
+  if (largest_first) *largest_first = w.sorted;
   return GN_OK;
 }
 

@@ -74,7 +74,7 @@ __global__ void k_powers_cf(const double *__restrict__ x, int32_t n, int32_t pma
 // KM: the longest support the launch handles (the forward products of one
 // monomial live in a KM-entry per-thread array)
 template <int L, int KM>
-__global__ void __launch_bounds__(128) k_monomials_cf(
+__global__ void __launch_bounds__(256) k_monomials_cf(
     const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
     const double *__restrict__ coef, int64_t T, const double *__restrict__ pow, int32_t n,
     double *__restrict__ stage_val, double *__restrict__ stage_d,
@@ -384,11 +384,12 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
     k_powers_cf<L><<<(unsigned)((a.nvar + 127) / 128), 128, 0, st>>>(a.x, (int32_t)a.nvar, a.pmax, a.pow,
                                                                       a.status);
   if (a.T > 0) {
+    const int bt = (a.block == 64 || a.block == 256) ? a.block : 128;
     if (a.kmax <= 16)
-      k_monomials_cf<L, 16><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
+      k_monomials_cf<L, 16><<<(unsigned)((a.T + bt - 1) / bt), bt, 0, st>>>(
           a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
     else
-      k_monomials_cf<L, KMAXI><<<(unsigned)((a.T + 127) / 128), 128, 0, st>>>(
+      k_monomials_cf<L, KMAXI><<<(unsigned)((a.T + bt - 1) / bt), bt, 0, st>>>(
           a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
   }
   if (a.nlong > 0)

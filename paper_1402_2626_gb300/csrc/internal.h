@@ -93,6 +93,7 @@ struct EvalArgs {
   const int64_t *f_out = nullptr;  // complex-entry offsets of f (or null: i)
   int neg_f = 0;
   const int32_t *status = nullptr;
+  int block = 128;  // CTA size of the per-term kernel (64, 128 or 256)
 };
 gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st);
 // whether the system's arithmetic evaluates (eval_int) or solves (lstsq) on

@@ -35,7 +35,8 @@ REPORT_MAX = 64
 SYMBOLS = ("gn_system_create", "gn_system_destroy", "gn_system_set_arith", "gn_system_info",
            "gn_eval", "gn_lstsq", "gn_mgs", "gn_newton", "gn_batch_create", "gn_batch_destroy",
            "gn_batch_info", "gn_batch_newton", "gn_status_str", "gn_version", "gn_eval_noalloc",
-           "gn_system_set_coef", "gn_adjoint", "gn_newton_mixed", "gn_set_wait_limit")
+           "gn_system_set_coef", "gn_adjoint", "gn_newton_mixed", "gn_set_wait_limit",
+           "gn_batch_tuning")
 # gn_arith: the faster per step (default), integer mantissas, or FP64
 # error-free transformations
 ARITH = {"auto": 0, "int": 1, "fp64": 2}
@@ -105,6 +106,8 @@ def load_library(path: str = LIB_PATH):
         L.gn_batch_info.restype = C.c_int
         L.gn_batch_newton.argtypes = [vp, C.c_int, vp, C.c_int32, vp, vp, vp]
         L.gn_batch_newton.restype = C.c_int
+        L.gn_batch_tuning.argtypes = [vp, C.c_int] + [C.POINTER(C.c_int32)] * 4
+        L.gn_batch_tuning.restype = C.c_int
         L.gn_set_wait_limit.argtypes = [C.c_int64, i64p]
         L.gn_set_wait_limit.restype = C.c_int
         L.gn_status_str.argtypes = [C.c_int]
@@ -295,6 +298,14 @@ class Batch:
         _check(self._lib.gn_batch_info(self._h, C.byref(S), C.byref(X), C.byref(T), C.byref(nnz),
                                        C.byref(mx)), "gn_batch_info")
         return dict(S=S.value, X=X.value, T=T.value, nnz=nnz.value, max_n=mx.value)
+
+    def tuning(self, prec):
+        """The launch choices of the first newton() call at ``prec`` (gn_batch_tuning)."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(self._lib.gn_batch_tuning(self._h, PREC[prec], *[C.byref(q) for q in v]),
+               "gn_batch_tuning")
+        return dict(eval_block=v[0].value, solve_threads=v[1].value, solve_grid=v[2].value,
+                    largest_first=bool(v[3].value))
 
     def newton(self, prec, x, steps, status, norms=None, stream=None):
         """``steps`` Gauss-Newton steps on every system, in place on x [X,2,L];
