@@ -46,9 +46,10 @@ FP64_LANES_PER_SM = 2
 IMAD_LANES_PER_SM = 64
 PRECS = {"d": 1, "dd": 2, "qd": 4}
 # DRAM bytes (read + write) of one k_mgs_int launch at 256 x 257, by limbs,
-# from a one-kernel ncu capture of the current kernel (null: no capture of
-# the current kernel at that precision)
-MGS_TRAFFIC = {}
+# from a one-kernel ncu capture of the current kernel with the L2 kept
+# between kernels (profiles/k_mgs_int_gn256_dram.md); null for a precision
+# without a capture of the current kernel
+MGS_TRAFFIC = {1: 132864 + 559360, 2: 202240 + 2200064, 4: 436480 + 3690496}
 # untimed steps run just before the timed region while the clocks are sampled
 SOAK_S = 1.0
 # kernels one Gauss-Newton step launches at n = 256 (integer arithmetic):

@@ -169,6 +169,7 @@ using namespace gn;
 
 extern "C" gn_status gn_adjoint(gn_system *s, gn_prec prec, const double *d_x, const double *d_g,
                                 double *d_grad, double *d_lambda, int32_t flags, void *cuda_stream) {
+  gn::Range nvtx_range("gn_adjoint");
   if (!s || (prec != 1 && prec != 2 && prec != 4) || !d_x || !d_g || (s->T > 0 && !d_grad) ||
       (flags & ~GN_ADJ_REUSE))
     return GN_EINVAL;

@@ -469,6 +469,7 @@ static int batch_occupancy(int threads) {
 // its work queue (largest systems first, or as stored), timed over one
 // solve of every system.  The fastest of each is kept.
 static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, cudaStream_t st) {
+  gn::Range nvtx_range("gn_batch_newton: tune launches");
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -558,6 +559,7 @@ static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, c
 
 static gn_status batch_capture(gn_batch *b, int L, BatchWs *w, double *d_x, double *norms, int32_t *status,
                                int32_t max_steps) {
+  gn::Range nvtx_range("gn_batch_newton: capture step graph");
   if (w->exec) {
     cudaGraphExecDestroy(w->exec);
     w->exec = nullptr;
@@ -600,6 +602,7 @@ extern "C" {
 gn_status gn_batch_create(gn_batch **out, int32_t S, const int64_t *h_sys_n, int64_t T,
                           const int64_t *h_poly_ptr, const int64_t *h_mono_ptr, const int32_t *h_var,
                           const uint8_t *h_exp, const double *h_coef, int32_t coef_limbs) {
+  gn::Range nvtx_range("gn_batch_create");
   if (!out) return GN_EINVAL;
   *out = nullptr;
   if (S < 1 || T < 0 || !h_sys_n || !h_poly_ptr || !h_mono_ptr || (T > 0 && !h_coef) ||
@@ -798,6 +801,7 @@ gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, 
 
 gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps, double *d_norms,
                           int32_t *d_status, void *cuda_stream) {
+  gn::Range nvtx_range("gn_batch_newton");
   if (!b || !(prec == 1 || prec == 2 || prec == 4) || !d_x || !d_status || steps < 1 || b->kmax > 64)
     return GN_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -122,6 +122,7 @@ gn_status gn_system_create(gn_system **out, int32_t N, int32_t n, int64_t T,
                            const int64_t *h_poly_ptr, const int64_t *h_mono_ptr,
                            const int32_t *h_var, const uint8_t *h_exp, const double *h_coef,
                            int32_t coef_limbs) {
+  gn::Range nvtx_range("gn_system_create");
   if (!out) return GN_EINVAL;
   *out = nullptr;
   if (n < 1 || N < n || T < 0 || n >= (1 << 24)) return GN_EINVAL;
@@ -253,6 +254,7 @@ gn_status gn_system_info(const gn_system *s, int32_t *N, int32_t *n, int64_t *T,
 
 gn_status gn_eval(gn_system *s, gn_prec prec, const double *d_x, double *d_f, double *d_J,
                   int64_t ldJ, void *cuda_stream) {
+  gn::Range nvtx_range("gn_eval");
   if (!s || !valid_prec(prec) || !d_x || (d_J && ldJ < s->N)) return GN_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   Workspace *ws;
@@ -279,6 +281,7 @@ gn_status gn_system_set_arith(gn_system *s, gn_arith arith) {
 
 gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                    double *d_R, double *d_dx, void *cuda_stream) {
+  gn::Range nvtx_range("gn_lstsq");
   if (!s || !valid_prec(prec) || n < 1 || m < n || ldAb < m || !d_Ab || !d_R || !d_dx)
     return GN_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;
@@ -329,6 +332,7 @@ gn_status gn_lstsq(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_A
 
 gn_status gn_mgs(gn_system *s, gn_prec prec, int32_t m, int32_t n, double *d_Ab, int64_t ldAb,
                  double *d_R, int32_t *d_status, void *cuda_stream) {
+  gn::Range nvtx_range("gn_mgs");
   if (!s || !valid_prec(prec) || n < 1 || n > s->n || m < n || ldAb < m || !d_Ab || !d_R ||
       !d_status)
     return GN_EINVAL;
@@ -366,6 +370,7 @@ static gn_status newton_step(gn_system *s, int L, Workspace *ws, double *d_x, cu
 }
 
 static gn_status build_graph(gn_system *s, int L, Workspace *ws, double *d_x) {
+  gn::Range nvtx_range("gn_newton: capture step graph");
   if (ws->step_exec) {
     cudaGraphExecDestroy(ws->step_exec);
     ws->step_exec = nullptr;
@@ -395,6 +400,7 @@ static gn_status build_graph(gn_system *s, int L, Workspace *ws, double *d_x) {
 
 extern "C" gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, double tol,
                                gn_report *report, void *cuda_stream) {
+  gn::Range nvtx_range("gn_newton");
   if (!s || !valid_prec(prec) || !d_x || steps < 1 || steps > GN_REPORT_MAX || !(tol >= 0.0))
     return GN_EINVAL;
   cudaStream_t st = (cudaStream_t)cuda_stream;

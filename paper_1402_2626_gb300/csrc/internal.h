@@ -2,11 +2,23 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/gn.h"
 
 namespace gn {
+
+// An NVTX range over a host-side phase of an entry point (named "gn_newton:
+// capture" and so on), for timelines of a profiler; without a profiler
+// attached the calls do nothing.  Device work inside a captured graph shows
+// under the kernels' own names.
+struct Range {
+  explicit Range(const char *name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range &) = delete;
+  Range &operator=(const Range &) = delete;
+};
 
 // One workspace per precision, allocated on first use.
 struct Workspace {

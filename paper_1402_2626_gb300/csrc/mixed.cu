@@ -155,6 +155,7 @@ using namespace gn;
 extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, int32_t d_steps,
                                      int32_t refine_steps, double tol, gn_report *report,
                                      void *cuda_stream) {
+  gn::Range nvtx_range("gn_newton_mixed");
   if (!s || (prec != GN_DD && prec != GN_QD) || !d_x || d_steps < 1 || refine_steps < 0 ||
       d_steps + refine_steps > GN_REPORT_MAX || !(tol >= 0.0))
     return GN_EINVAL;
