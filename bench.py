@@ -47,8 +47,8 @@ IMAD_LANES_PER_SM = 64
 PRECS = {"d": 1, "dd": 2, "qd": 4}
 # DRAM bytes (read + write) of one k_mgs_int launch at 256 x 257, by limbs,
 # from a one-kernel ncu capture of the current kernel with the L2 kept
-# between kernels (profiles/k_mgs_int_gn256_dram.md); null for a precision
-# without a capture of the current kernel
+# between kernels (--only mgs under ncu); null for a precision without a
+# capture of the current kernel
 MGS_TRAFFIC = {1: 132864 + 559360, 2: 202240 + 2200064, 4: 436480 + 3690496}
 # untimed steps run just before the timed region while the clocks are sampled
 SOAK_S = 1.0
@@ -356,7 +356,8 @@ def run_section(args):
     torch.cuda.set_device(dev)
     build.build()
     flush = torch.empty(2 * L2_BYTES, dtype=torch.uint8, device=dev)
-    fn = {"eval": lambda: eval_section(dev, flush, args),
+    fn = {"rates": lambda: measured_rates(),
+          "eval": lambda: eval_section(dev, flush, args),
           "mgs": lambda: mgs_section(dev, flush, args),
           "adjoint": lambda: adjoint_extra(dev, flush, args),
           "mixed": lambda: mixed_extra(dev, flush, args),
@@ -478,7 +479,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip per-precision breakdowns")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched configuration")
-    ap.add_argument("--only", choices=["eval", "mgs", "adjoint", "mixed", "paper", "batched"],
+    ap.add_argument("--only", choices=["rates", "eval", "mgs", "adjoint", "mixed", "paper", "batched"],
                     help="run one extra section alone and print it as the JSON line (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
