@@ -192,6 +192,12 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  *      [J, -f] = Q R (Section 3) frozen: b = -f(x) at precision prec
  *      (Section 2), y = Q^H b in double, R dx = y in double, x <- x + dx at
  *      precision prec.
+ * Under GN_ARITH_INT or GN_ARITH_AUTO with 32 <= n <= 1024 the double
+ * factorisation is CholeskyQR: R from the Cholesky factor of the exact Gram
+ * matrix of [J, -f] (integer mantissas), Q never formed, and the refinement's
+ * y = R^-H (J^H b); its error, about kappa(J)^2 u_double, suits Jacobians with
+ * kappa(J)^2 u_double << 1, and a pivot below 2^-20 of its column's norm is
+ * reported as GN_ESINGULAR.  Otherwise the double phase is MGS.
  * Phase 2 gains about -log10(kappa(J) u_double) digits per step, so for a
  * consistent system (f(x*) = 0) it reaches the root at precision prec:
  * quad double from a double start takes three or four steps for

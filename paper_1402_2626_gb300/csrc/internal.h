@@ -152,6 +152,12 @@ inline size_t bs_inv_doubles(int32_t n, int L) {
   return (size_t)((n + 15) / 16) * 256 * (2 * (size_t)L + 1);
 }
 constexpr int BACKSUB_INT_MAX_N = 1024;
+// CholeskyQR of [A b] (double complex, N x (n+1), leading dimension N) for the
+// mixed solver: R (double, upper, leading dimension n+1) and its mantissa
+// form (Rm, Zs, the column exponents in rinv) for the integer solves
+bool cholqr_available(const gn_system *s);
+gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, double *Rm,
+                        double *Zs, int32_t *status, cudaStream_t st);
 // R and 1/r_kk as cascades from the mantissas the MGS launch left
 gn_status launch_mgs_r_out(int L, double *R, const double *Rm, int64_t ldr, int32_t ncols,
                            double *rinv, const int32_t *status, cudaStream_t st);

@@ -17,6 +17,14 @@
 // system this is the root at precision L.  The factorisation, the cost the
 // paper finds dominant, runs once per double step instead of once per step
 // at precision L.
+//
+// With the integer arithmetic and 32 .. 1024 unknowns the double
+// factorisation is CholeskyQR (cholqr.cu) instead of MGS: each double step
+// is the evaluation, the exact Gram matrix of [J, -f], its Cholesky factor
+// (whose last column is y = R^-H J^H (-f)), R dx = y and x += dx; each
+// refinement forms c = J^H b with the frozen J, R^H w = c, then R dx = w
+// (the normal equations through the Cholesky factor, kappa(J)^2 u_double
+// per step, which the refinement tolerates for kappa(J)^2 u << 1).
 #include <string.h>
 
 #include "internal.h"
@@ -90,11 +98,51 @@ __global__ void __launch_bounds__(MIX_THREADS) k_mix_qhb(const double *__restric
   }
 }
 
-// y (double complex, column n of the cascade R) into column n of the
-// mantissas Rm as one-limb fixed point at a common scale 2^sig, |y| / 2^sig
-// < 2^61 (the format MGS leaves its last column in), sig into sexp[n]; one
-// CTA.
-__global__ void __launch_bounds__(MIX_THREADS) k_mix_y_fixed(const double *__restrict__ R,
+// c_k = sum_i conj(a_ik) b_i in double for the frozen J (column-major, ld N)
+// and b = the leading limbs of -f (stored at precision L), into c; CTA 0
+// also forms ||f||_2 (leading limbs).  One CTA per column k, partial sums
+// over rows i = tid, tid + 256, ... added in a fixed tree.
+template <int L>
+__global__ void __launch_bounds__(MIX_THREADS) k_mix_ahb(const double *__restrict__ A, int64_t lda,
+                                                         int32_t m, const double *__restrict__ negf,
+                                                         double *__restrict__ c, double *__restrict__ fnorm,
+                                                         const int32_t *__restrict__ status) {
+  __shared__ double sre[MIX_THREADS], sim[MIX_THREADS], sf[MIX_THREADS];
+  if (*status != GN_OK) return;
+  const int k = blockIdx.x;
+  double re = 0.0, im = 0.0, ff = 0.0;
+  for (int i = threadIdx.x; i < m; i += MIX_THREADS) {
+    const double ar = A[((int64_t)k * lda + i) * 2], ai = A[((int64_t)k * lda + i) * 2 + 1];
+    const double br = negf[(int64_t)i * 2 * L], bi = negf[(int64_t)i * 2 * L + L];
+    re = fma(ar, br, fma(ai, bi, re));
+    im = fma(ar, bi, fma(-ai, br, im));
+    ff = fma(br, br, fma(bi, bi, ff));
+  }
+  sre[threadIdx.x] = re;
+  sim[threadIdx.x] = im;
+  sf[threadIdx.x] = ff;
+  __syncthreads();
+#pragma unroll
+  for (int h = MIX_THREADS / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      sre[threadIdx.x] += sre[threadIdx.x + h];
+      sim[threadIdx.x] += sim[threadIdx.x + h];
+      sf[threadIdx.x] += sf[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    c[2 * k] = sre[0];
+    c[2 * k + 1] = sim[0];
+    if (k == 0) *fnorm = sqrt(sf[0]);
+  }
+}
+
+// y (double complex, y_i at y + 2 i: column n of the cascade R, or a
+// vector) into column n of the mantissas Rm as one-limb fixed point at a
+// common scale 2^sig, |y| / 2^sig < 2^61 (the format MGS leaves its last
+// column in), sig into sexp[n]; one CTA.
+__global__ void __launch_bounds__(MIX_THREADS) k_mix_y_fixed(const double *__restrict__ yv,
                                                             double *__restrict__ Rm, int64_t ldr,
                                                             int32_t n, double *__restrict__ sexp,
                                                             const int32_t *__restrict__ status) {
@@ -102,7 +150,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_mix_y_fixed(const double *__res
   if (*status != GN_OK) return;
   double m = 0.0;
   for (int i = threadIdx.x; i < n; i += MIX_THREADS) {
-    const double *y = R + ((int64_t)n * ldr + i) * 2;
+    const double *y = yv + 2 * (int64_t)i;
     m = fmax(m, fmax(fabs(y[0]), fabs(y[1])));
   }
   smax[threadIdx.x] = m;
@@ -115,7 +163,7 @@ __global__ void __launch_bounds__(MIX_THREADS) k_mix_y_fixed(const double *__res
   if (smax[0] > 0.0) frexp(smax[0], &e);  // max |y| < 2^e
   const int sig = e - 61;
   for (int i = threadIdx.x; i < n; i += MIX_THREADS) {
-    const double *y = R + ((int64_t)n * ldr + i) * 2;
+    const double *y = yv + 2 * (int64_t)i;
     long long *d = (long long *)(Rm + ((int64_t)n * ldr + i) * 2);
     d[0] = llrint(ldexp(y[0], -sig));
     d[1] = llrint(ldexp(y[1], -sig));
@@ -138,7 +186,8 @@ static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double 
     // the integer factors of the last double step are still in place: the
     // blocked back substitution on them
     double *sexp = w1->rinv + 2 * (size_t)(n + 1);
-    k_mix_y_fixed<<<1, MIX_THREADS, 0, st>>>(w1->R, w1->Rm, n + 1, n, sexp, wL->status);
+    k_mix_y_fixed<<<1, MIX_THREADS, 0, st>>>(w1->R + (int64_t)n * (n + 1) * 2, w1->Rm, n + 1, n, sexp,
+                                             wL->status);
     e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, wL->status, st);
   } else {
     e = launch_backsub_fp64(1, w1->R, n + 1, n, w1->rinv, w1->dx, wL->status, st);
@@ -146,6 +195,64 @@ static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double 
   if (e) return e;
   k_mix_spread<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, w1->dx, wL->dx);
   return launch_update(L, n, d_x, wL->dx, fnorm, wL->norms, wL->status, st);
+}
+
+// One refinement step with the frozen CholeskyQR factors of the last double
+// step (cholqr.cu): b = -f(x) at precision L, c = J^H b, R^H w = c, R dx = w
+// (both blocked solves on the factor's mantissas), x += dx at precision L.
+template <int L>
+static gn_status refine_step_cq(gn_system *s, Workspace *w1, Workspace *wL, double *d_x, cudaStream_t st) {
+  const int32_t N = s->N, n = s->n;
+  const int64_t W = 2 * L;
+  double *negf = wL->Ab + (int64_t)n * N * W;
+  double *fnorm = wL->rinv;
+  double *c = w1->lam, *w = wL->lam;  // [n] double complex each (lam holds N >= n entries)
+  double *sexp = w1->rinv + 2 * (size_t)(n + 1);
+  gn_status e = launch_eval_sel(s, L, d_x, negf, 1, nullptr, N, st);
+  if (e) return e;
+  k_mix_ahb<L><<<(unsigned)n, MIX_THREADS, 0, st>>>(w1->Ab, N, N, negf, c, fnorm, wL->status);
+  e = launch_fwdsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, c, w, wL->status, st);
+  if (e) return e;
+  k_mix_y_fixed<<<1, MIX_THREADS, 0, st>>>(w, w1->Rm, n + 1, n, sexp, wL->status);
+  e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, wL->status, st);
+  if (e) return e;
+  k_mix_spread<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, w1->dx, wL->dx);
+  return launch_update(L, n, d_x, wL->dx, fnorm, wL->norms, wL->status, st);
+}
+
+// d_steps Gauss-Newton steps in double on w1->xmix with CholeskyQR
+// factorisations: evaluation into [J, -f], the factor R of [J, -f] (its last
+// column is y), R dx = y, x += dx; the factors of the last step stay in w1.
+static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_report *r1,
+                              cudaStream_t st) {
+  const int32_t N = s->N, n = s->n;
+  w1->fact = 0;
+  if (cudaMemsetAsync(w1->status, 0, sizeof(int32_t) * 2, st) != cudaSuccess ||
+      cudaMemsetAsync(w1->norms, 0, sizeof(double) * 3 * GN_REPORT_MAX, st) != cudaSuccess)
+    return GN_ECUDA;
+  const double *fnorm = w1->rinv + (n + 1) + n;  // ||b|| = ||f||: the b column's norm
+  for (int32_t k = 0; k < d_steps; k++) {
+    gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, st);
+    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->Rm, w1->Zs, w1->status, st);
+    if (!e)
+      e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, w1->status, st);
+    if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, st);
+    if (e) return e;
+  }
+  if (cudaMemcpyAsync(w1->h_status, w1->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(w1->h_norms, w1->norms, sizeof(double) * 3 * GN_REPORT_MAX, cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return GN_ECUDA;
+  memset(r1, 0, sizeof(*r1));
+  r1->status = w1->h_status[0];
+  r1->steps_done = w1->h_status[1];
+  for (int32_t k = 0; k < r1->steps_done && k < GN_REPORT_MAX; k++) {
+    r1->res_norm[k] = w1->h_norms[3 * k];
+    r1->dx_norm[k] = w1->h_norms[3 * k + 1];
+  }
+  return (gn_status)w1->h_status[0];
 }
 
 }  // namespace gn
@@ -175,7 +282,8 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
   }
   if (cudaPeekAtLastError() != cudaSuccess) return GN_ECUDA;
   gn_report r1;
-  e = gn_newton(s, GN_D, w1->xmix, d_steps, 0.0, &r1, cuda_stream);
+  const bool cq = cholqr_available(s);
+  e = cq ? cholqr_steps(s, w1, d_steps, &r1, st) : gn_newton(s, GN_D, w1->xmix, d_steps, 0.0, &r1, cuda_stream);
   if (report) {
     report->steps_done = r1.steps_done;
     for (int k = 0; k < r1.steps_done; k++) {
@@ -185,15 +293,15 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
     report->status = e;
   }
   if (e) return e;
-  // the last step's factors as doubles
+  // the last step's factors as doubles (MGS), or in place (CholeskyQR)
   const bool int_fact = w1->fact == 1;
-  if (w1->fact == 1) {
+  if (!cq && w1->fact == 1) {
     e = launch_mgs_to_cascade(1, w1->Ab, s->N, s->N, n + 1, w1->rinv, w1->status, st);
     if (!e) e = launch_mgs_r_out(1, w1->R, w1->Rm, n + 1, n + 1, w1->rinv, w1->status, st);
     if (e) return e;
     w1->fact = 2;
   }
-  if (w1->fact != 2) return GN_EINVAL;
+  if (!cq && w1->fact != 2) return GN_EINVAL;
   switch (L) {
     case 2: k_mix_spread<2><<<nb, 128, 0, st>>>(n, w1->xmix, d_x); break;
     case 4: k_mix_spread<4><<<nb, 128, 0, st>>>(n, w1->xmix, d_x); break;
@@ -205,7 +313,10 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
     return GN_ECUDA;
   bool converged = false;
   for (int32_t k = 0; k < refine_steps; k++) {
-    e = L == 2 ? refine_step<2>(s, w1, wL, d_x, int_fact, st) : refine_step<4>(s, w1, wL, d_x, int_fact, st);
+    if (cq)
+      e = L == 2 ? refine_step_cq<2>(s, w1, wL, d_x, st) : refine_step_cq<4>(s, w1, wL, d_x, st);
+    else
+      e = L == 2 ? refine_step<2>(s, w1, wL, d_x, int_fact, st) : refine_step<4>(s, w1, wL, d_x, int_fact, st);
     if (e) return e;
     if (tol > 0.0) {
       if (cudaMemcpyAsync(wL->h_status, wL->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=
