@@ -60,31 +60,48 @@ __device__ __forceinline__ void cq_tile(int t, int &ib, int &jb) {
   ib = t - j * (j + 1) / 2;
 }
 
+// acc (128-bit two's complement) += (hi, lo), one carry chain
+__device__ __forceinline__ void cq_add(uint64_t (&acc)[2], uint64_t lo, uint64_t hi) {
+  asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(acc[0]), "+l"(acc[1]) : "l"(lo), "l"(hi));
+}
+
+// acc += a b for signed 64-bit a, b: the 128-bit product from one low and one
+// signed high multiply
+__device__ __forceinline__ void cq_mac(uint64_t (&acc)[2], int64_t a, int64_t b) {
+  cq_add(acc, (uint64_t)a * (uint64_t)b, (uint64_t)__mul64hi(a, b));
+}
+
 // G_ij = sum_r conj(a_ri) a_rj for i <= j (the upper triangle of G, column-
 // major, leading dimension nc), exactly: the entries as 62-bit mantissas at
-// their columns' scales, each product 124 bits, the sums (N < 2^30 terms) in
-// three limbs, rounded to a double once at the end.  One CTA per 32 x 32
-// tile (ib <= jb) of 256 threads, thread (ty, tx) owning entries
-// (2 ty + {0,1}, 2 tx + {0,1}); rows in chunks of 32 staged in shared memory
-// as mantissas.
+// their columns' scales (fx_add_double: |M| < 2^62 and, the scale coming
+// from the column norm, sum_r |M_r|^2 < 2^124), the sums in 128-bit
+// accumulators, rounded to a double once at the end.  Each complex product
+// takes three real ones (Gauss): with s = ar - ai on the i side and
+// d1 = bi - br, d2 = br + bi on the j side (all below 2^63),
+//   conj(a) b = (br s + ai d2) + i (br s + ar d1),
+// exact in integers.  By Cauchy-Schwarz every partial sum of br s, of ai d2
+// and of ar d1 over rows is below 2^124.5 (|s|^2, |d1|^2, |d2|^2 sum to at
+// most twice the column's), so each accumulated part stays below 2^126 and
+// the 128-bit two's complement never wraps, for any N.  One CTA per 32 x 32 tile (ib <= jb) of 256 threads,
+// thread (ty, tx) owning entries (2 ty + {0,1}, 2 tx + {0,1}); rows in
+// chunks of 32 staged in shared memory as mantissas with those sums.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_gram(const double *__restrict__ A, int32_t N, int32_t nc,
                                                         const double *__restrict__ sexp,
                                                         double *__restrict__ G,
                                                         const int32_t *__restrict__ status) {
-  __shared__ int64_t sI[CQ_T][CQ_T][2];  // [row][column of the i tile][re, im]
-  __shared__ int64_t sJ[CQ_T][CQ_T][2];
+  __shared__ int64_t sI[CQ_T][CQ_T][3];  // [row][column of the i tile]: ar, ai, ar - ai
+  __shared__ int64_t sJ[CQ_T][CQ_T][3];  // [row][column of the j tile]: br, bi - br, br + bi
   if (*status != GN_OK) return;
   int ib, jb;
   cq_tile(blockIdx.x, ib, jb);
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  fx<3> cr[2][2], ci[2][2];
+  uint64_t cr[2][2][2], ci[2][2][2];
 #pragma unroll
   for (int a = 0; a < 2; a++)
 #pragma unroll
-    for (int b = 0; b < 2; b++) {
-      fx_zero<3>(cr[a][b]);
-      fx_zero<3>(ci[a][b]);
-    }
+    for (int b = 0; b < 2; b++)
+#pragma unroll
+      for (int w = 0; w < 2; w++) cr[a][b][w] = ci[a][b][w] = 0;
   for (int r0 = 0; r0 < N; r0 += CQ_T) {
     // stage rows r0 .. r0+31 of both tiles' columns: consecutive threads take
     // consecutive rows of one column (coalesced complex loads)
@@ -104,31 +121,41 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_gram(const double *__restrict
           fx_add_double<1>(mr, e[0], F);
           fx_add_double<1>(mi, e[1], F);
         }
-        int64_t(*dst)[CQ_T][2] = side ? sJ : sI;
-        dst[rr][cc][0] = (int64_t)mr.w[0];
-        dst[rr][cc][1] = (int64_t)mi.w[0];
+        const int64_t xr = (int64_t)mr.w[0], xi = (int64_t)mi.w[0];
+        if (side) {
+          sJ[rr][cc][0] = xr;
+          sJ[rr][cc][1] = xi - xr;
+          sJ[rr][cc][2] = xr + xi;
+        } else {
+          sI[rr][cc][0] = xr;
+          sI[rr][cc][1] = xi;
+          sI[rr][cc][2] = xr - xi;
+        }
       }
     }
     __syncthreads();
 #pragma unroll 4
     for (int rr = 0; rr < CQ_T; rr++) {
-      fx<1> ar[2], ai[2], br[2], bi[2];
+      int64_t ar[2], ai[2], as[2], br[2], d1[2], d2[2];
 #pragma unroll
       for (int a = 0; a < 2; a++) {
-        ar[a].w[0] = (uint64_t)sI[rr][2 * ty + a][0];
-        ai[a].w[0] = (uint64_t)sI[rr][2 * ty + a][1];
-        br[a].w[0] = (uint64_t)sJ[rr][2 * tx + a][0];
-        bi[a].w[0] = (uint64_t)sJ[rr][2 * tx + a][1];
+        ar[a] = sI[rr][2 * ty + a][0];
+        ai[a] = sI[rr][2 * ty + a][1];
+        as[a] = sI[rr][2 * ty + a][2];
+        br[a] = sJ[rr][2 * tx + a][0];
+        d1[a] = sJ[rr][2 * tx + a][1];
+        d2[a] = sJ[rr][2 * tx + a][2];
       }
 #pragma unroll
       for (int a = 0; a < 2; a++)
 #pragma unroll
         for (int b = 0; b < 2; b++) {
-          // conj(a) b = (ar br + ai bi) + i (ar bi - ai br)
-          cr[a][b] = ix_add<3>(cr[a][b], ix_widen<2, 3>(ix_mul_full<1, 1>(ar[a], br[b])));
-          cr[a][b] = ix_add<3>(cr[a][b], ix_widen<2, 3>(ix_mul_full<1, 1>(ai[a], bi[b])));
-          ci[a][b] = ix_add<3>(ci[a][b], ix_widen<2, 3>(ix_mul_full<1, 1>(ar[a], bi[b])));
-          ci[a][b] = ix_sub<3>(ci[a][b], ix_widen<2, 3>(ix_mul_full<1, 1>(ai[a], br[b])));
+          const uint64_t lo = (uint64_t)br[b] * (uint64_t)as[a];  // br s, shared by both parts
+          const uint64_t hi = (uint64_t)__mul64hi(br[b], as[a]);
+          cq_add(cr[a][b], lo, hi);
+          cq_add(ci[a][b], lo, hi);
+          cq_mac(cr[a][b], ai[a], d2[b]);
+          cq_mac(ci[a][b], ar[a], d1[b]);
         }
     }
     __syncthreads();
@@ -140,9 +167,17 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_gram(const double *__restrict
       const int i = ib * CQ_T + 2 * ty + a, j = jb * CQ_T + 2 * tx + b;
       if (i < nc && j < nc && i <= j) {
         const int F = -((int)sexp[i] + (int)sexp[j]);
+        fx<3> vr, vi;
+#pragma unroll
+        for (int w = 0; w < 2; w++) {
+          vr.w[w] = cr[a][b][w];
+          vi.w[w] = ci[a][b][w];
+        }
+        vr.w[2] = (uint64_t)((int64_t)cr[a][b][1] >> 63);  // sign extension
+        vi.w[2] = (uint64_t)((int64_t)ci[a][b][1] >> 63);
         double re[1], im[1];
-        fx_to_cascade<3, 1>(cr[a][b], F, re);
-        fx_to_cascade<3, 1>(ci[a][b], F, im);
+        fx_to_cascade<3, 1>(vr, F, re);
+        fx_to_cascade<3, 1>(vi, F, im);
         G[((int64_t)j * nc + i) * 2] = re[0];
         G[((int64_t)j * nc + i) * 2 + 1] = im[0];
       }
@@ -150,13 +185,23 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_gram(const double *__restrict
 }
 
 // The panel's diagonal block G[p:pe, p:pe] = R11^H R11 (upper, in place) by
-// one CTA in shared memory: for each k, r_kk = sqrt(g_kk), row k divided by
-// r_kk, the block's trailing upper triangle less conj(r_ki) r_kj.  A pivot
-// g_kk <= 2^-40 ||a_k||^2 (k < nchk) records GN_ESINGULAR.
+// one CTA in shared memory, right-looking: after row k is final (r_kk =
+// sqrt(g_kk), the rest of the row divided by r_kk), every g_ij with
+// k < i <= j less conj(r_ki) r_kj.  The pairs (i, j), 1 <= i <= j < 32, are
+// listed by decreasing i, so the pairs still to update after row k are the
+// first (31 - k)(32 - k) / 2 of the list and a step's threads are packed
+// into whole warps (the FP64 pipe, not the barriers, sets the pace of the
+// block).  The thread of pair (k + 1, k + 1) takes the next pivot as soon as
+// it has updated it.  A pivot g_kk <= 2^-40 ||a_k||^2 (k < nchk) records
+// GN_ESINGULAR.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G, int32_t nc, int32_t p,
                                                          const double *__restrict__ nrm0, int32_t nchk,
                                                          int32_t *__restrict__ status) {
+  constexpr int NPAIR = (CQ_T - 1) * CQ_T / 2;  // 496 pairs with i >= 1
+  static_assert(NPAIR <= 2 * CQ_THREADS, "two pairs per thread");
   __shared__ double2 sB[CQ_T][CQ_T];  // [row][column]
+  __shared__ unsigned short sPair[NPAIR];  // i << 8 | j
+  __shared__ double sInv[CQ_T];
   __shared__ int sBad;
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p);
@@ -170,40 +215,49 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
     }
     sB[i][j] = v;
   }
+  if (tid >= 1 && tid < CQ_T) {  // row i = tid starts after the rows below it
+    const int i = tid, base = (CQ_T - 1 - i) * (CQ_T - i) / 2;
+    for (int j = i; j < CQ_T; j++) sPair[base + j - i] = (unsigned short)(i << 8 | j);
+  }
   if (tid == 0) sBad = 0;
   __syncthreads();
-  for (int k = 0; k < pb; k++) {
-    if (tid == 0) {
-      const double d = sB[k][k].x;
-      const double n0 = nrm0[p + k];
-      const bool bad = !(d > ldexp(n0 * n0, -40));
-      if (bad && p + k < nchk) {
-        atomicCAS(status, GN_OK, GN_ESINGULAR);
-        sBad = 1;
-      }
-      const double r = d > 0.0 ? sqrt(d) : 0.0;
-      sB[k][k] = make_double2(r, 0.0);
+  // the pivot of row k (its thread only): r_kk, 1 / r_kk, the rank test
+  auto pivot = [&](int k) {
+    const double d = sB[k][k].x;
+    const bool bad = !(d > ldexp(nrm0[p + k] * nrm0[p + k], -40));
+    if (bad && p + k < nchk) {
+      atomicCAS(status, GN_OK, GN_ESINGULAR);
+      sBad = 1;
     }
+    const double inv = d > 0.0 ? rsqrt(d) : 0.0;
+    sB[k][k] = make_double2(d * inv, 0.0);
+    sInv[k] = inv;
+  };
+  if (tid == 0) pivot(0);
+  for (int k = 0;; k++) {
     __syncthreads();
     if (sBad) return;  // uniform: read after the barrier
-    const double r = sB[k][k].x;
-    const double inv = r > 0.0 ? 1.0 / r : 0.0;
-    for (int j = k + 1 + tid; j < pb; j += CQ_THREADS) {
+    const double inv = sInv[k];
+    for (int j = k + 1 + tid; j < CQ_T; j += CQ_THREADS) {
       sB[k][j].x *= inv;
       sB[k][j].y *= inv;
     }
+    if (k + 1 >= pb) break;
     __syncthreads();
-    // g_ij -= conj(r_ki) r_kj for k < i <= j < pb
-    for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
-      const int i = q % CQ_T, j = q / CQ_T;
-      if (i > k && i <= j && j < pb) {
+    const int np = (CQ_T - 1 - k) * (CQ_T - k) / 2, qk = (CQ_T - 2 - k) * (CQ_T - 1 - k) / 2;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int q = tid + h * CQ_THREADS;
+      if (q < np) {
+        const int pr = sPair[q], i = pr >> 8, j = pr & 255;
         const double2 a = sB[k][i], b = sB[k][j];
         sB[i][j].x -= a.x * b.x + a.y * b.y;
         sB[i][j].y -= a.x * b.y - a.y * b.x;
+        if (q == qk) pivot(k + 1);  // pair (k + 1, k + 1)
       }
     }
-    __syncthreads();
   }
+  __syncthreads();
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
     if (i < pb && j < pb && i <= j) {
@@ -220,6 +274,7 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, int32_t nc, int32_t p,
                                                         const int32_t *__restrict__ status) {
   __shared__ double2 sR[CQ_T][CQ_T];
+  __shared__ double sInv[CQ_T];
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p), pe = p + pb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -233,6 +288,8 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, 
     sR[i][j] = v;
   }
   __syncthreads();
+  if (tid < CQ_T) sInv[tid] = sR[tid][tid].x > 0.0 ? 1.0 / sR[tid][tid].x : 0.0;
+  __syncthreads();
   const int j = pe + blockIdx.x * (CQ_THREADS / 32) + warp;
   if (j >= nc) return;  // whole warps
   double *col = G + (int64_t)j * nc * 2;
@@ -240,8 +297,7 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, 
   if (lane < pb) g = make_double2(col[2 * (p + lane)], col[2 * (p + lane) + 1]);
   for (int i = 0; i < pb; i++) {
     // x_i = g_i / r_ii (r_ii real), then g_k -= conj(r_ik) x_i for k > i
-    const double rii = sR[i][i].x;
-    const double inv = rii > 0.0 ? 1.0 / rii : 0.0;
+    const double inv = sInv[i];
     double2 xi = make_double2(0.0, 0.0);
     if (lane == i) {
       g.x *= inv;
