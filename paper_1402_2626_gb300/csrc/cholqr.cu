@@ -7,8 +7,10 @@
 // double factorisation per double Gauss-Newton step.  For a tall matrix MGS
 // (Section 3) is a chain of n dependent pivots whose bulk updates of the
 // later columns set its pace; here the O(m n^2) work becomes one
-// throughput-bound contraction on the integer pipe (the exact Gram matrix of
-// the columns' 62-bit mantissas), and only an O(n^3 / 3) Cholesky in FP64 is
+// throughput-bound contraction, the exact Gram matrix of the columns'
+// mantissas: on the tensor cores as products of 7-bit digit planes
+// (gram_tc.cu, the columns rounded to 56 bits), else on the integer pipe
+// (k_cq_gram below, 62 bits), and only an O(n^3 / 3) Cholesky in FP64 is
 // left.  The factor's last column is y = R^-H A^H b and R_nn = ||b - A x||,
 // as MGS on [A b] gives them (eq. 2), so the Gauss-Newton step and the
 // refinement's y = R^-H (A^H b) reuse the blocked integer triangular solves
@@ -412,13 +414,18 @@ bool cholqr_available(const gn_system *s) {
 }
 
 gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, double *Rm,
-                        double *Zs, int32_t *status, cudaStream_t st) {
+                        double *Zs, void *scratch, int32_t *status, cudaStream_t st) {
   const int32_t nc = n + 1;
   double *nrm0 = rinv + nc, *sexp = rinv + 2 * (size_t)nc;  // the layout of the one-limb rinv
   k_cq_scale<<<(unsigned)((nc * 32 + CQ_THREADS - 1) / CQ_THREADS), CQ_THREADS, 0, st>>>(A, N, nc, nrm0,
                                                                                       sexp, status);
-  const int nb = (nc + CQ_T - 1) / CQ_T;
-  k_cq_gram<<<(unsigned)(nb * (nb + 1) / 2), CQ_THREADS, 0, st>>>(A, N, nc, sexp, R, status);
+  if (scratch && gram_tc_available(N, nc)) {
+    const gn_status e = launch_gram_tc(N, nc, A, sexp, R, scratch, status, st);
+    if (e) return e;
+  } else {
+    const int nb = (nc + CQ_T - 1) / CQ_T;
+    k_cq_gram<<<(unsigned)(nb * (nb + 1) / 2), CQ_THREADS, 0, st>>>(A, N, nc, sexp, R, status);
+  }
   for (int p = 0; p < nc; p += CQ_T) {
     k_cq_potrf<<<1, CQ_THREADS, 0, st>>>(R, nc, p, nrm0, n, status);
     const int pe = p + CQ_T < nc ? p + CQ_T : nc;

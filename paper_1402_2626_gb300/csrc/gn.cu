@@ -50,6 +50,7 @@ static void ws_free(Workspace &w) {
   cudaFree(w.Rm);
   cudaFree(w.Zs);
   cudaFree(w.Xinv);
+  cudaFree(w.cq_scratch);
   if (w.h_norms) cudaFreeHost(w.h_norms);
   if (w.h_status) cudaFreeHost(w.h_status);
   w = Workspace();

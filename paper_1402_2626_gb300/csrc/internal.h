@@ -38,6 +38,8 @@ struct Workspace {
   double *Rm = nullptr;         // mantissas of R (layout of R)
   double *Zs = nullptr;         // [(n+1) (L+1)] mantissas and exponents of 1/r_jj
   double *Xinv = nullptr;       // inverses of R's 16 x 16 diagonal blocks (blocked back substitution)
+  void *cq_scratch = nullptr;   // CholeskyQR's tensor-core Gram scratch (allocated on first use)
+  size_t cq_bytes = 0;
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
   // what Ab, R, Rm, Zs and rinv hold: 0 nothing reusable; 1 / 2 the
@@ -157,7 +159,15 @@ constexpr int BACKSUB_INT_MAX_N = 1024;
 // form (Rm, Zs, the column exponents in rinv) for the integer solves
 bool cholqr_available(const gn_system *s);
 gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, double *Rm,
-                        double *Zs, int32_t *status, cudaStream_t st);
+                        double *Zs, void *scratch, int32_t *status, cudaStream_t st);
+// The Gram matrix G = A^H A (upper triangle, double complex, leading
+// dimension nc) of A (N x nc, leading dimension N) on the tensor cores,
+// exact for the columns rounded to 56 bits at their scales 2^sexp_j;
+// scratch of gram_tc_scratch_bytes (digit planes and per-pair products)
+bool gram_tc_available(int32_t N, int32_t nc);
+size_t gram_tc_scratch_bytes(int32_t N, int32_t nc);
+gn_status launch_gram_tc(int32_t N, int32_t nc, const double *A, const double *sexp, double *G, void *scratch,
+                         int32_t *status, cudaStream_t st);
 // R and 1/r_kk as cascades from the mantissas the MGS launch left
 gn_status launch_mgs_r_out(int L, double *R, const double *Rm, int64_t ldr, int32_t ncols,
                            double *rinv, const int32_t *status, cudaStream_t st);

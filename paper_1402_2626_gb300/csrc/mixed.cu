@@ -231,9 +231,20 @@ static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_r
       cudaMemsetAsync(w1->norms, 0, sizeof(double) * 3 * GN_REPORT_MAX, st) != cudaSuccess)
     return GN_ECUDA;
   const double *fnorm = w1->rinv + (n + 1) + n;  // ||b|| = ||f||: the b column's norm
+  // scratch of the tensor-core Gram matrix, kept with the workspace; without
+  // it (no memory) the Gram matrix is formed on the integer pipe
+  if (gram_tc_available(N, n + 1) && !w1->cq_scratch) {
+    const size_t need = gram_tc_scratch_bytes(N, n + 1);
+    if (cudaMalloc(&w1->cq_scratch, need) == cudaSuccess) {
+      w1->cq_bytes = need;
+    } else {
+      cudaGetLastError();
+      w1->cq_scratch = nullptr;
+    }
+  }
   for (int32_t k = 0; k < d_steps; k++) {
     gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, st);
-    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->Rm, w1->Zs, w1->status, st);
+    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->Rm, w1->Zs, w1->cq_scratch, w1->status, st);
     if (!e)
       e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, w1->status, st);
     if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, st);
