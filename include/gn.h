@@ -299,7 +299,7 @@ gn_status gn_batch_info(const gn_batch *b, int32_t *S, int64_t *X, int64_t *T, i
  *   d_norms  : [steps][S][2] device doubles (may be NULL): ||f(x_k)|| and
  *              ||dx_k|| of each system at each step.
  * Stream-ordered; does not synchronize.  The first call per precision tunes
- * the launch on the batch (gn_batch_tuning: three evaluations and up to four
+ * the launch on the batch (gn_batch_tuning: six evaluations and up to four
  * solves on a copy of x, synchronizing) and keeps the fastest choices.
  */
 gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps, double *d_norms,
@@ -310,6 +310,9 @@ gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps,
  * by timing the candidates on the batch (host-owned outputs, any may be
  * NULL):
  *   eval_block    : CTA size of the per-term evaluation kernel (64, 128, 256);
+ *   eval_lanes    : lanes per term of that kernel: 1 (the product chain of
+ *                   Section 2.2 on one lane) or 2 (its forward and backward
+ *                   products on a lane pair);
  *   solve_threads : CTA size of the persistent solver (128 or 256);
  *   solve_grid    : its CTAs (SMs x resident CTAs);
  *   largest_first : 1 when its work queue takes the largest systems first,
@@ -318,8 +321,8 @@ gn_status gn_batch_newton(gn_batch *b, gn_prec prec, double *d_x, int32_t steps,
  * not yet stepped.  Batching and its tuning are this library's, not the
  * paper's.
  */
-gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, int32_t *solve_threads,
-                          int32_t *solve_grid, int32_t *largest_first);
+gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, int32_t *eval_lanes,
+                          int32_t *solve_threads, int32_t *solve_grid, int32_t *largest_first);
 
 /*
  * gn_eval_noalloc — the same evaluation as gn_eval, for callers that may not

@@ -40,6 +40,7 @@ struct BatchWs {
   int32_t *counter = nullptr;  // [0] work queue position, [1] step index
   int threads = 0, grid = 0;   // tuned launch of the solver
   int eval_block = 128;        // tuned CTA size of the per-term evaluation kernel
+  int eval_lanes = 1;          // tuned lanes per term of that kernel (1 or 2)
   int sorted = 1;              // solver queue: largest systems first (1) or as stored (0)
   cudaGraphExec_t exec = nullptr;
   const double *gx = nullptr;
@@ -428,6 +429,7 @@ static gn_status batch_eval(gn_batch *b, int L, BatchWs *w, const double *d_x, c
   a.neg_f = 1;
   a.status = w->zero;
   a.block = w->eval_block;
+  a.lanes = w->eval_lanes;
   return launch_eval_int_raw(L, a, st);
 }
 
@@ -493,12 +495,13 @@ static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, c
       return GN_ECUDA;
     return GN_OK;
   };
-  // 1. the evaluation kernel's CTA size
-  const int ecand[3] = {64, 128, 256};
+  // 1. the evaluation kernel's lanes per term and CTA size
+  const int ecand[6][2] = {{1, 64}, {1, 128}, {1, 256}, {2, 64}, {2, 128}, {2, 256}};
   float best = 1e30f;
-  int eb = 128;
-  for (int c = 0; c < 3 && !e; c++) {
-    w->eval_block = ecand[c];
+  int eb = 128, el = 1;
+  for (int c = 0; c < 6 && !e; c++) {
+    w->eval_lanes = ecand[c][0];
+    w->eval_block = ecand[c][1];
     e = reset();
     if (!e) e = batch_eval(b, L, w, xs, st);  // warm-up
     if (e) break;
@@ -509,9 +512,11 @@ static gn_status batch_tune(gn_batch *b, int L, BatchWs *w, const double *d_x, c
     if (!e) e = elapsed(ms);
     if (!e && ms < best) {
       best = ms;
-      eb = ecand[c];
+      el = ecand[c][0];
+      eb = ecand[c][1];
     }
   }
+  w->eval_lanes = el;
   w->eval_block = eb;
   // 2. the solver's CTA size and queue order
   const int cand[2] = {128, 256};
@@ -787,12 +792,13 @@ gn_status gn_batch_info(const gn_batch *b, int32_t *S, int64_t *X, int64_t *T, i
   return GN_OK;
 }
 
-gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, int32_t *solve_threads,
-                          int32_t *solve_grid, int32_t *largest_first) {
+gn_status gn_batch_tuning(const gn_batch *b, gn_prec prec, int32_t *eval_block, int32_t *eval_lanes,
+                          int32_t *solve_threads, int32_t *solve_grid, int32_t *largest_first) {
   if (!b || !(prec == 1 || prec == 2 || prec == 4)) return GN_EINVAL;
   const BatchWs &w = b->ws[prec];
   if (!w.threads) return GN_EINVAL;  // not tuned yet
   if (eval_block) *eval_block = w.eval_block;
+  if (eval_lanes) *eval_lanes = w.eval_lanes;
   if (solve_threads) *solve_threads = w.threads;
   if (solve_grid) *solve_grid = w.grid;
   if (largest_first) *largest_first = w.sorted;

@@ -118,6 +118,100 @@ __global__ void __launch_bounds__(256) k_monomials_cf(
   }
 }
 
+// the value of the other lane of a pair (lanes 2p, 2p + 1 of the warp)
+template <int K>
+__device__ __forceinline__ cf<K> cf_pair_swap(const cf<K> &a) {
+  const unsigned mask = 3u << (threadIdx.x & 30);
+  cf<K> r;
+#pragma unroll
+  for (int w = 0; w < K; w++) {
+    r.re.w[w] = __shfl_xor_sync(mask, (unsigned long long)a.re.w[w], 1);
+    r.im.w[w] = __shfl_xor_sync(mask, (unsigned long long)a.im.w[w], 1);
+  }
+  r.e = __shfl_xor_sync(mask, a.e, 1);
+  return r;
+}
+
+// The schedule of k_monomials_cf on a lane pair per term, the same products
+// in the same order (so the same bits), with the two chains side by side:
+// lane 0 of the pair forms the coefficient times the common factor and the
+// forward products F_s = a x_0 .. x_{s-1}; lane 1 the backward products
+// B_s = x_{s+1} .. x_{k-1} (the running product from the end).  Then the
+// pair forms the partials d_s F_s B_s two at a time, lane 0 the even s and
+// lane 1 the odd s, each taking the factor it lacks from the other lane by
+// one shuffle.  The dependent chain per term is the common factor plus k - 1
+// products plus k / 2, against the common factor plus 3k - 3 on one lane.
+template <int L, int KM>
+__global__ void __launch_bounds__(256) k_monomials2_cf(
+    const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
+    const double *__restrict__ coef, int64_t T, const double *__restrict__ pow, int32_t n,
+    double *__restrict__ stage_val, double *__restrict__ stage_d,
+    const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t t = g >> 1;
+  const int side = (int)(g & 1);
+  if (t >= T || *status != GN_OK) return;  // both lanes of a pair alike
+  const int o0 = __ldg(mono_off + t);
+  const int k = __ldg(mono_off + t + 1) - o0;
+  if (k > KM) return;  // a long support: k_monomials_long_cf
+  cf<L> P[KM];  // lane 0: F_s; lane 1: B_s
+  if (side == 0) {
+    double cre[L], cim[L];
+#pragma unroll
+    for (int l = 0; l < L; l++) {
+      cre[l] = __ldg(coef + (int64_t)(2 * l + 0) * T + t);
+      cim[l] = __ldg(coef + (int64_t)(2 * l + 1) * T + t);
+    }
+    cf<L> a = cf_from_cascade<L, L>(cre, cim);
+    for (int s = 0; s < k; s++) {
+      uint32_t w = __ldg(occ + o0 + s);
+      int d = (int)(w & 255u);
+      if (d >= 2) a = cf_mul<L>(a, cf_ld<L>(pow + ((int64_t)(d - 2) * n + (w >> 8)) * WS));
+    }
+    if (k == 0) {
+      cf_st<L>(stage_val + t * WS, a);
+      return;
+    }
+    P[0] = a;
+    for (int s = 1; s < k; s++) {
+      int v = (int)(__ldg(occ + o0 + s - 1) >> 8);
+      P[s] = cf_mul<L>(P[s - 1], cf_ld<L>(pow + (int64_t)v * WS));
+    }
+    const uint32_t wl = __ldg(occ + o0 + k - 1);
+    cf_st<L>(stage_val + t * WS, cf_mul<L>(P[k - 1], cf_ld<L>(pow + (int64_t)(wl >> 8) * WS)));
+  } else {
+    if (k == 0) return;
+    if (k >= 2) {
+      cf<L> B = cf_ld<L>(pow + (int64_t)(__ldg(occ + o0 + k - 1) >> 8) * WS);
+      for (int s = k - 2; s >= 0; s--) {
+        P[s] = B;
+        if (s > 0) B = cf_mul<L>(B, cf_ld<L>(pow + (int64_t)(__ldg(occ + o0 + s) >> 8) * WS));
+      }
+    }
+  }
+  // partials: step q takes s0 = 2q on lane 0 and s1 = 2q + 1 on lane 1; lane 0
+  // sends F_s1, lane 1 sends B_s0 (what the other lane lacks)
+  for (int s0 = 0; s0 < k; s0 += 2) {
+    const int s1 = s0 + 1;
+    const int mine = side == 0 ? s0 : s1;
+    const int give = side == 0 ? s1 : s0;
+    const cf<L> got = cf_pair_swap<L>(P[give < k ? give : mine]);
+    if (mine >= k) continue;
+    const uint32_t w = __ldg(occ + o0 + mine);
+    // lane 0 holds F_mine and receives B_mine; lane 1 holds B_mine and receives F_mine
+    const cf<L> F = side == 0 ? P[mine] : got;
+    cf<L> dv;
+    if (mine == k - 1) {
+      dv = cf_scale_d<L>(F, w & 255u);  // B_{k-1} is the empty product
+    } else {
+      const cf<L> B = side == 0 ? got : P[mine];
+      dv = cf_scale_d<L>(cf_mul<L>(F, B), w & 255u);
+    }
+    cf_st<L>(stage_d + (int64_t)(o0 + mine) * WS, dv);
+  }
+}
+
 // a cf<K> value and whether it holds anything (the empty product)
 template <int K>
 struct cfo {
@@ -385,12 +479,27 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
                                                                       a.status);
   if (a.T > 0) {
     const int bt = (a.block == 64 || a.block == 256) ? a.block : 128;
-    if (a.kmax <= 16)
-      k_monomials_cf<L, 16><<<(unsigned)((a.T + bt - 1) / bt), bt, 0, st>>>(
-          a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
-    else
-      k_monomials_cf<L, KMAXI><<<(unsigned)((a.T + bt - 1) / bt), bt, 0, st>>>(
-          a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+    // one lane per term where the product chain is short (the kernel is
+    // bound by its ALU instructions: gn256, k = 16, DD 0.205 ms against
+    // 0.260 ms on pairs), a lane pair where it is long (k = 40, DD 0.148
+    // against 0.173 ms); batches time both
+    const int lanes = a.lanes == 1 || a.lanes == 2 ? a.lanes : (a.kmax <= 16 ? 1 : 2);
+    const unsigned nb = (unsigned)((lanes * a.T + bt - 1) / bt);
+    if (lanes == 1) {
+      if (a.kmax <= 16)
+        k_monomials_cf<L, 16><<<nb, bt, 0, st>>>(a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar,
+                                                 a.stage_val, a.stage_d, a.status);
+      else
+        k_monomials_cf<L, KMAXI><<<nb, bt, 0, st>>>(a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar,
+                                                    a.stage_val, a.stage_d, a.status);
+    } else {
+      if (a.kmax <= 16)
+        k_monomials2_cf<L, 16><<<nb, bt, 0, st>>>(a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar,
+                                                  a.stage_val, a.stage_d, a.status);
+      else
+        k_monomials2_cf<L, KMAXI><<<nb, bt, 0, st>>>(a.mono_off, a.occ, a.coef, a.T, a.pow,
+                                                     (int32_t)a.nvar, a.stage_val, a.stage_d, a.status);
+    }
   }
   if (a.nlong > 0)
     k_monomials_long_cf<L><<<(unsigned)((a.nlong + 3) / 4), 128, 0, st>>>(

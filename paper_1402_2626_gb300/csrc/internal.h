@@ -108,6 +108,10 @@ struct EvalArgs {
   int neg_f = 0;
   const int32_t *status = nullptr;
   int block = 128;  // CTA size of the per-term kernel (64, 128 or 256)
+  // lanes per term of the integer per-term kernel: 1, 2 (the forward and
+  // backward products side by side), or 0 to choose by the longest support
+  // (1 up to 16 variables, 2 beyond)
+  int lanes = 0;
 };
 gn_status launch_eval_int_raw(int L, const EvalArgs &a, cudaStream_t st);
 // whether the system's arithmetic evaluates (eval_int) or solves (lstsq) on

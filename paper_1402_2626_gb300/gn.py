@@ -106,7 +106,7 @@ def load_library(path: str = LIB_PATH):
         L.gn_batch_info.restype = C.c_int
         L.gn_batch_newton.argtypes = [vp, C.c_int, vp, C.c_int32, vp, vp, vp]
         L.gn_batch_newton.restype = C.c_int
-        L.gn_batch_tuning.argtypes = [vp, C.c_int] + [C.POINTER(C.c_int32)] * 4
+        L.gn_batch_tuning.argtypes = [vp, C.c_int] + [C.POINTER(C.c_int32)] * 5
         L.gn_batch_tuning.restype = C.c_int
         L.gn_set_wait_limit.argtypes = [C.c_int64, i64p]
         L.gn_set_wait_limit.restype = C.c_int
@@ -301,11 +301,11 @@ class Batch:
 
     def tuning(self, prec):
         """The launch choices of the first newton() call at ``prec`` (gn_batch_tuning)."""
-        v = [C.c_int32() for _ in range(4)]
+        v = [C.c_int32() for _ in range(5)]
         _check(self._lib.gn_batch_tuning(self._h, PREC[prec], *[C.byref(q) for q in v]),
                "gn_batch_tuning")
-        return dict(eval_block=v[0].value, solve_threads=v[1].value, solve_grid=v[2].value,
-                    largest_first=bool(v[3].value))
+        return dict(eval_block=v[0].value, eval_lanes=v[1].value, solve_threads=v[2].value,
+                    solve_grid=v[3].value, largest_first=bool(v[4].value))
 
     def newton(self, prec, x, steps, status, norms=None, stream=None):
         """``steps`` Gauss-Newton steps on every system, in place on x [X,2,L];

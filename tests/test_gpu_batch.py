@@ -118,6 +118,7 @@ def test_batch_full_size_sampled():
     # the tuner's choices are among its candidates
     tune = g.tuning("dd")
     assert tune["eval_block"] in (64, 128, 256) and tune["solve_threads"] in (128, 256)
+    assert tune["eval_lanes"] in (1, 2)
     assert tune["solve_grid"] % torch.cuda.get_device_properties(0).multi_processor_count == 0
     with pytest.raises(gn.GnError):
         g.tuning("qd")  # never stepped in QD
