@@ -12,8 +12,12 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 CASES = [
+    # 32 unknowns: CholeskyQR with the Gram matrix on the tensor cores
     ("overdetermined", dict(N=48, n=32, M=(8, 16), k=(1, 6), dmax=4, seed=601)),
+    # below 32 unknowns: the integer MGS double step
     ("square", dict(N=24, n=24, M=(8, 24), k=(1, 5), dmax=3, seed=602)),
+    # above 2048 rows: CholeskyQR with the Gram matrix on the integer pipe
+    ("tall", dict(N=2100, n=32, M=(3, 6), k=(1, 4), dmax=3, seed=603)),
 ]
 
 
