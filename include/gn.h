@@ -193,11 +193,19 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  *      (Section 2), y = Q^H b in double, R dx = y in double, x <- x + dx at
  *      precision prec.
  * Under GN_ARITH_INT or GN_ARITH_AUTO with 32 <= n <= 1024 the double
- * factorisation is CholeskyQR: R from the Cholesky factor of the exact Gram
- * matrix of [J, -f] (integer mantissas), Q never formed, and the refinement's
- * y = R^-H (J^H b); its error, about kappa(J)^2 u_double, suits Jacobians with
+ * factorisation is CholeskyQR: R from the Cholesky factor (FP64) of the Gram
+ * matrix of [J, -f], Q never formed, and the refinement's y = R^-H (J^H b);
+ * its error, about kappa(J)^2 u_double, suits Jacobians with
  * kappa(J)^2 u_double << 1, and a pivot below 2^-20 of its column's norm is
- * reported as GN_ESINGULAR.  Otherwise the double phase is MGS.
+ * reported as GN_ESINGULAR.  The Gram matrix is exact for the columns
+ * rounded at their scales, then rounded once to doubles: on the tensor
+ * cores (BF16 products of 7-bit digit planes, 56-bit columns) for N <= 2048,
+ * else on the integer pipe (62-bit columns).  The first such call on a
+ * system allocates the tensor-core form's scratch, kept until
+ * gn_system_destroy: 32 Np nq + 2^22 nb (nb + 1) bytes (Np = N rounded up to
+ * 64, nb = ceil((n+1)/128), nq = 128 nb; 434 MB at N = 1536, n = 1024); if
+ * it cannot be allocated the integer-pipe form runs instead.  Otherwise the
+ * double phase is MGS.
  * Phase 2 gains about -log10(kappa(J) u_double) digits per step, so for a
  * consistent system (f(x*) = 0) it reaches the root at precision prec:
  * quad double from a double start takes three or four steps for
