@@ -193,11 +193,12 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  *      (Section 2), y = Q^H b in double, R dx = y in double, x <- x + dx at
  *      precision prec.
  * Under GN_ARITH_INT or GN_ARITH_AUTO with 32 <= n <= 1024 the double
- * factorisation is CholeskyQR: R from the Cholesky factor (FP64) of the Gram
- * matrix of [J, -f], Q never formed, and the refinement's y = R^-H (J^H b);
- * its error, about kappa(J)^2 u_double, suits Jacobians with
- * kappa(J)^2 u_double << 1, and a pivot below 2^-20 of its column's norm is
- * reported as GN_ESINGULAR.  The Gram matrix is exact for the columns
+ * factorisation is CholeskyQR: R from the Cholesky factor of the Gram
+ * matrix of [J, -f] (scaled by its columns' powers of two, in float-float
+ * arithmetic on the FP32 pipe: about 47 significant bits), Q never formed,
+ * and the refinement's y = R^-H (J^H b); its error, about kappa(J)^2 2^-47,
+ * suits Jacobians with kappa(J)^2 2^-47 << 1, and a pivot below 2^-20 of its
+ * column's norm is reported as GN_ESINGULAR.  The Gram matrix is exact for the columns
  * rounded at their scales, then rounded once to doubles: on the tensor
  * cores (BF16 products of 7-bit digit planes, 56-bit columns) for N <= 2048,
  * else on the integer pipe (62-bit columns).  The first such call on a

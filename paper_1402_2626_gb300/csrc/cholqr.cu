@@ -10,8 +10,8 @@
 // throughput-bound contraction, the exact Gram matrix of the columns'
 // mantissas: on the tensor cores as products of 7-bit digit planes
 // (gram_tc.cu, the columns rounded to 56 bits), else on the integer pipe
-// (k_cq_gram below, 62 bits), and only an O(n^3 / 3) Cholesky in FP64 is
-// left.  The factor's last column is y = R^-H A^H b and R_nn = ||b - A x||,
+// (k_cq_gram below, 62 bits), and only an O(n^3 / 3) Cholesky is left, in
+// float-float on the FP32 pipe (below).  The factor's last column is y = R^-H A^H b and R_nn = ||b - A x||,
 // as MGS on [A b] gives them (eq. 2), so the Gauss-Newton step and the
 // refinement's y = R^-H (A^H b) reuse the blocked integer triangular solves
 // (bsb.cuh) once R is in their mantissa format.
@@ -186,35 +186,129 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_gram(const double *__restrict
     }
 }
 
-// The panel's diagonal block G[p:pe, p:pe] = R11^H R11 (upper, in place) by
-// one CTA in shared memory, right-looking: after row k is final (r_kk =
-// sqrt(g_kk), the rest of the row divided by r_kk), every g_ij with
+// ---- float-float arithmetic on the FP32 pipe ----
+//
+// The Cholesky runs on values h + l of two floats (about 47 significant
+// bits): GB300 issues 64 FP32 lanes for every FP64 lane, and the refinement
+// needs the double factors only to contract (their error, about
+// kappa^2 2^-47, stays far below the contraction the frozen Jacobian
+// allows).  Sums follow Knuth's TwoSum with Dekker's renormalisation,
+// products the FMA form of Dekker's TwoProduct (Dekker 1971; Knuth, TAOCP
+// vol. 2, 4.2.2).  The Gram matrix is scaled by its columns' powers of two
+// first, G^_ij = G_ij 2^-(s_i + 62) 2^-(s_j + 62), so every entry lies in
+// [-1, 1] and the float exponent range holds it; then R = R^ D with
+// D = diag(2^(s_j + 62)).
+
+struct ffv {
+  float h, l;
+};
+struct cff {
+  ffv re, im;
+};
+
+__device__ __forceinline__ ffv ff_from(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+
+__device__ __forceinline__ double ff_to(ffv a) { return (double)a.h + (double)a.l; }
+
+// (the _rn intrinsics are never fused into FMAs, which would break the
+// error terms)
+__device__ __forceinline__ ffv ff_add(ffv a, ffv b) {
+  const float s = __fadd_rn(a.h, b.h), bb = __fsub_rn(s, a.h);
+  float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+__device__ __forceinline__ ffv ff_neg(ffv a) { return {-a.h, -a.l}; }
+
+__device__ __forceinline__ ffv ff_mul(ffv a, ffv b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = fmaf(a.h, b.h, -p);
+  e = fmaf(a.h, b.l, e);
+  e = fmaf(a.l, b.h, e);
+  const float h = __fadd_rn(p, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// 1 / sqrt(d) for d > 0: the FP32 estimate and two Newton steps
+// y <- y + y (1 - d y^2) / 2 in float-float
+__device__ __forceinline__ ffv ff_rsqrt(ffv d) {
+  ffv y = {rsqrtf(d.h), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const ffv e = ff_add({1.f, 0.f}, ff_neg(ff_mul(d, ff_mul(y, y))));
+    const ffv t = ff_mul(y, e);
+    y = ff_add(y, {__fmul_rn(0.5f, t.h), __fmul_rn(0.5f, t.l)});
+  }
+  return y;
+}
+
+// g -= conj(a) b
+__device__ __forceinline__ void cff_sub_conj_mul(cff &g, const cff &a, const cff &b) {
+  const ffv re = ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im));
+  const ffv im = ff_add(ff_mul(a.re, b.im), ff_neg(ff_mul(a.im, b.re)));
+  g.re = ff_add(g.re, ff_neg(re));
+  g.im = ff_add(g.im, ff_neg(im));
+}
+
+__device__ __forceinline__ cff cff_scale(const cff &a, ffv s) { return {ff_mul(a.re, s), ff_mul(a.im, s)}; }
+
+// one complex entry of the scaled matrix: four floats where the double
+// complex entry was
+__device__ __forceinline__ cff cff_ld(const double *G, int64_t at) {
+  const float4 v = *(const float4 *)(G + at * 2);
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+
+__device__ __forceinline__ void cff_st(double *G, int64_t at, const cff &a) {
+  *(float4 *)(G + at * 2) = make_float4(a.re.h, a.re.l, a.im.h, a.im.l);
+}
+
+// G (double complex, upper triangle, leading dimension nc) into G^ in
+// float-float, in place; thread per entry of the upper triangle's columns
+__global__ void k_cq_to_ff(double *__restrict__ G, int32_t nc, const double *__restrict__ sexp,
+                           const int32_t *__restrict__ status) {
+  if (*status != GN_OK) return;
+  const int j = blockIdx.x;
+  const int sj = (int)sexp[j] + CQ_S;
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const int64_t at = (int64_t)j * nc + i;
+    const int sc = -(sj + (int)sexp[i] + CQ_S);
+    const double re = ldexp(G[at * 2], sc), im = ldexp(G[at * 2 + 1], sc);
+    cff_st(G, at, {ff_from(re), ff_from(im)});
+  }
+}
+
+// The panel's diagonal block G^[p:pe, p:pe] = R11^H R11 (upper, in place)
+// by one CTA in shared memory, right-looking: after row k is final (r_kk =
+// sqrt(g_kk), the rest of the row times 1 / r_kk), every g_ij with
 // k < i <= j less conj(r_ki) r_kj.  The pairs (i, j), 1 <= i <= j < 32, are
 // listed by decreasing i, so the pairs still to update after row k are the
 // first (31 - k)(32 - k) / 2 of the list and a step's threads are packed
-// into whole warps (the FP64 pipe, not the barriers, sets the pace of the
-// block).  The thread of pair (k + 1, k + 1) takes the next pivot as soon as
-// it has updated it.  A pivot g_kk <= 2^-40 ||a_k||^2 (k < nchk) records
-// GN_ESINGULAR.
+// into whole warps.  The thread of pair (k + 1, k + 1) takes the next pivot
+// as soon as it has updated it.  A pivot g_kk <= 2^-40 ||a_k||^2 (k < nchk;
+// in the scaled units) records GN_ESINGULAR.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G, int32_t nc, int32_t p,
-                                                         const double *__restrict__ nrm0, int32_t nchk,
+                                                         const double *__restrict__ nrm0,
+                                                         const double *__restrict__ sexp, int32_t nchk,
                                                          int32_t *__restrict__ status) {
   constexpr int NPAIR = (CQ_T - 1) * CQ_T / 2;  // 496 pairs with i >= 1
   static_assert(NPAIR <= 2 * CQ_THREADS, "two pairs per thread");
-  __shared__ double2 sB[CQ_T][CQ_T];  // [row][column]
+  __shared__ cff sB[CQ_T][CQ_T];           // [row][column]
   __shared__ unsigned short sPair[NPAIR];  // i << 8 | j
-  __shared__ double sInv[CQ_T];
+  __shared__ ffv sInv[CQ_T];
   __shared__ int sBad;
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p);
   const int tid = threadIdx.x;
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
-    double2 v = make_double2(0.0, 0.0);
-    if (i < pb && j < pb && i <= j) {
-      const double *e = G + ((int64_t)(p + j) * nc + p + i) * 2;
-      v = make_double2(e[0], e[1]);
-    }
+    cff v = {{0.f, 0.f}, {0.f, 0.f}};
+    if (i < pb && j < pb && i <= j) v = cff_ld(G, (int64_t)(p + j) * nc + p + i);
     sB[i][j] = v;
   }
   if (tid >= 1 && tid < CQ_T) {  // row i = tid starts after the rows below it
@@ -225,25 +319,23 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   __syncthreads();
   // the pivot of row k (its thread only): r_kk, 1 / r_kk, the rank test
   auto pivot = [&](int k) {
-    const double d = sB[k][k].x;
-    const bool bad = !(d > ldexp(nrm0[p + k] * nrm0[p + k], -40));
+    const ffv d = sB[k][k].re;
+    const float n0 = (float)ldexp(nrm0[p + k], -((int)sexp[p + k] + CQ_S));  // in (1/2, 1]
+    const bool bad = !(d.h > ldexpf(n0 * n0, -40));
     if (bad && p + k < nchk) {
       atomicCAS(status, GN_OK, GN_ESINGULAR);
       sBad = 1;
     }
-    const double inv = d > 0.0 ? rsqrt(d) : 0.0;
-    sB[k][k] = make_double2(d * inv, 0.0);
+    const ffv inv = d.h > 0.f ? ff_rsqrt(d) : ffv{0.f, 0.f};
+    sB[k][k] = {ff_mul(d, inv), {0.f, 0.f}};
     sInv[k] = inv;
   };
   if (tid == 0) pivot(0);
   for (int k = 0;; k++) {
     __syncthreads();
     if (sBad) return;  // uniform: read after the barrier
-    const double inv = sInv[k];
-    for (int j = k + 1 + tid; j < CQ_T; j += CQ_THREADS) {
-      sB[k][j].x *= inv;
-      sB[k][j].y *= inv;
-    }
+    const ffv inv = sInv[k];
+    for (int j = k + 1 + tid; j < CQ_T; j += CQ_THREADS) sB[k][j] = cff_scale(sB[k][j], inv);
     if (k + 1 >= pb) break;
     __syncthreads();
     const int np = (CQ_T - 1 - k) * (CQ_T - k) / 2, qk = (CQ_T - 2 - k) * (CQ_T - 1 - k) / 2;
@@ -252,9 +344,9 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
       const int q = tid + h * CQ_THREADS;
       if (q < np) {
         const int pr = sPair[q], i = pr >> 8, j = pr & 255;
-        const double2 a = sB[k][i], b = sB[k][j];
-        sB[i][j].x -= a.x * b.x + a.y * b.y;
-        sB[i][j].y -= a.x * b.y - a.y * b.x;
+        cff g = sB[i][j];
+        cff_sub_conj_mul(g, sB[k][i], sB[k][j]);
+        sB[i][j] = g;
         if (q == qk) pivot(k + 1);  // pair (k + 1, k + 1)
       }
     }
@@ -262,72 +354,61 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   __syncthreads();
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
-    if (i < pb && j < pb && i <= j) {
-      double *e = G + ((int64_t)(p + j) * nc + p + i) * 2;
-      e[0] = sB[i][j].x;
-      e[1] = sB[i][j].y;
-    }
+    if (i < pb && j < pb && i <= j) cff_st(G, (int64_t)(p + j) * nc + p + i, sB[i][j]);
   }
 }
 
 // The panel's rows to the right of its diagonal block: R12 = R11^-H G12, by
 // forward substitution with R11^H (lower): one warp per column j >= pe,
-// lane i holding row p + i; R11 staged in shared memory by each CTA.
+// lane i holding row p + i; R11 and the reciprocals of its diagonal staged
+// in shared memory by each CTA.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, int32_t nc, int32_t p,
                                                         const int32_t *__restrict__ status) {
-  __shared__ double2 sR[CQ_T][CQ_T];
-  __shared__ double sInv[CQ_T];
+  __shared__ cff sR[CQ_T][CQ_T];
+  __shared__ ffv sInv[CQ_T];
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p), pe = p + pb;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
-    double2 v = make_double2(0.0, 0.0);
-    if (i < pb && j < pb && i <= j) {
-      const double *e = G + ((int64_t)(p + j) * nc + p + i) * 2;
-      v = make_double2(e[0], e[1]);
-    }
+    cff v = {{0.f, 0.f}, {0.f, 0.f}};
+    if (i < pb && j < pb && i <= j) v = cff_ld(G, (int64_t)(p + j) * nc + p + i);
     sR[i][j] = v;
   }
   __syncthreads();
-  if (tid < CQ_T) sInv[tid] = sR[tid][tid].x > 0.0 ? 1.0 / sR[tid][tid].x : 0.0;
+  if (tid < CQ_T) {
+    const ffv r = sR[tid][tid].re;
+    sInv[tid] = r.h > 0.f ? ff_mul(ff_rsqrt(r), ff_rsqrt(r)) : ffv{0.f, 0.f};  // 1 / r_ii
+  }
   __syncthreads();
   const int j = pe + blockIdx.x * (CQ_THREADS / 32) + warp;
   if (j >= nc) return;  // whole warps
-  double *col = G + (int64_t)j * nc * 2;
-  double2 g = make_double2(0.0, 0.0);
-  if (lane < pb) g = make_double2(col[2 * (p + lane)], col[2 * (p + lane) + 1]);
+  cff g = {{0.f, 0.f}, {0.f, 0.f}};
+  if (lane < pb) g = cff_ld(G, (int64_t)j * nc + p + lane);
   for (int i = 0; i < pb; i++) {
     // x_i = g_i / r_ii (r_ii real), then g_k -= conj(r_ik) x_i for k > i
-    const double inv = sInv[i];
-    double2 xi = make_double2(0.0, 0.0);
+    cff xi = {{0.f, 0.f}, {0.f, 0.f}};
     if (lane == i) {
-      g.x *= inv;
-      g.y *= inv;
+      g = cff_scale(g, sInv[i]);
       xi = g;
     }
-    xi.x = __shfl_sync(0xffffffffu, xi.x, i);
-    xi.y = __shfl_sync(0xffffffffu, xi.y, i);
-    if (lane > i && lane < pb) {
-      const double2 a = sR[i][lane];  // r_i,lane
-      g.x -= a.x * xi.x + a.y * xi.y;
-      g.y -= a.x * xi.y - a.y * xi.x;
-    }
+    xi.re.h = __shfl_sync(0xffffffffu, xi.re.h, i);
+    xi.re.l = __shfl_sync(0xffffffffu, xi.re.l, i);
+    xi.im.h = __shfl_sync(0xffffffffu, xi.im.h, i);
+    xi.im.l = __shfl_sync(0xffffffffu, xi.im.l, i);
+    if (lane > i && lane < pb) cff_sub_conj_mul(g, sR[i][lane], xi);  // r_i,lane
   }
-  if (lane < pb) {
-    col[2 * (p + lane)] = g.x;
-    col[2 * (p + lane) + 1] = g.y;
-  }
+  if (lane < pb) cff_st(G, (int64_t)j * nc + p + lane, g);
 }
 
-// The trailing matrix: G_ij -= sum_{k in the panel} conj(r_ki) r_kj for
+// The trailing matrix: G^_ij -= sum_{k in the panel} conj(r_ki) r_kj for
 // pe <= i <= j < nc, by 32 x 32 tiles (ib <= jb over the trailing range), 256
 // threads of 2 x 2 entries, the panel's rows of both tiles' columns staged
 // in shared memory.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, int32_t nc, int32_t p,
                                                         const int32_t *__restrict__ status) {
-  __shared__ double2 sI[CQ_T][CQ_T];  // [panel row][column of the i tile]
-  __shared__ double2 sJ[CQ_T][CQ_T];
+  __shared__ cff sI[CQ_T][CQ_T];  // [panel row][column of the i tile]
+  __shared__ cff sJ[CQ_T][CQ_T];
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p), pe = p + pb;
   int ib, jb;
@@ -336,35 +417,25 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, 
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int k = q % CQ_T, c = q / CQ_T;
-    double2 u = make_double2(0.0, 0.0), v = make_double2(0.0, 0.0);
+    cff u = {{0.f, 0.f}, {0.f, 0.f}}, v = u;
     if (k < pb) {
-      if (i0 + c < nc) {
-        const double *e = G + ((int64_t)(i0 + c) * nc + p + k) * 2;
-        u = make_double2(e[0], e[1]);
-      }
-      if (j0 + c < nc) {
-        const double *e = G + ((int64_t)(j0 + c) * nc + p + k) * 2;
-        v = make_double2(e[0], e[1]);
-      }
+      if (i0 + c < nc) u = cff_ld(G, (int64_t)(i0 + c) * nc + p + k);
+      if (j0 + c < nc) v = cff_ld(G, (int64_t)(j0 + c) * nc + p + k);
     }
     sI[k][c] = u;
     sJ[k][c] = v;
   }
   __syncthreads();
-  double2 acc[2][2];
+  cff acc[2][2];
 #pragma unroll
   for (int a = 0; a < 2; a++)
 #pragma unroll
-    for (int b = 0; b < 2; b++) acc[a][b] = make_double2(0.0, 0.0);
+    for (int b = 0; b < 2; b++) acc[a][b] = {{0.f, 0.f}, {0.f, 0.f}};
   for (int k = 0; k < pb; k++) {
 #pragma unroll
     for (int a = 0; a < 2; a++)
 #pragma unroll
-      for (int b = 0; b < 2; b++) {
-        const double2 u = sI[k][2 * ty + a], v = sJ[k][2 * tx + b];
-        acc[a][b].x = fma(u.x, v.x, fma(u.y, v.y, acc[a][b].x));
-        acc[a][b].y = fma(u.x, v.y, fma(-u.y, v.x, acc[a][b].y));
-      }
+      for (int b = 0; b < 2; b++) cff_sub_conj_mul(acc[a][b], sI[k][2 * ty + a], sJ[k][2 * tx + b]);
   }
 #pragma unroll
   for (int a = 0; a < 2; a++)
@@ -372,33 +443,34 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, 
     for (int b = 0; b < 2; b++) {
       const int i = i0 + 2 * ty + a, j = j0 + 2 * tx + b;
       if (i < nc && j < nc && i <= j) {
-        double *e = G + ((int64_t)j * nc + i) * 2;
-        e[0] -= acc[a][b].x;
-        e[1] -= acc[a][b].y;
+        const int64_t at = (int64_t)j * nc + i;
+        cff g = cff_ld(G, at);
+        g.re = ff_add(g.re, acc[a][b].re);  // acc holds minus the sum
+        g.im = ff_add(g.im, acc[a][b].im);
+        cff_st(G, at, g);
       }
     }
 }
 
-// R (double, upper, leading dimension nc) into the mantissa format of the
-// integer triangular solves: column j's entries as one-limb mantissas at
-// 2^s_j (|r_kj| <= ||a_j|| < 2^(62 + s_j)), 1/r_jj as a mantissa in
-// [2^61, 2^62) and its exponent (Zs), 1/r_jj as a double too.  One CTA per
-// column.
+// R = R^ D (R^ in float-float, upper, leading dimension nc) into the
+// mantissa format of the integer triangular solves: column j's entries as
+// one-limb mantissas at 2^s_j (r_kj 2^-s_j = r^_kj 2^62, |r^_kj| <= 1), 1/r_jj
+// as a mantissa in [2^61, 2^62) and its exponent (Zs), 1/r_jj as a double
+// too.  One CTA per column.
 __global__ void k_cq_to_int(const double *__restrict__ R, int32_t nc, const double *__restrict__ sexp,
                             double *__restrict__ Rm, double *__restrict__ Zs, double *__restrict__ rinv,
                             const int32_t *__restrict__ status) {
   if (*status != GN_OK) return;
   const int j = blockIdx.x;
-  const int F = -(int)sexp[j];
   for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-    const double *e = R + ((int64_t)j * nc + k) * 2;
+    const cff e = cff_ld(R, (int64_t)j * nc + k);
     long long *d = (long long *)(Rm + ((int64_t)j * nc + k) * 2);
-    d[0] = llrint(ldexp(e[0], F));
-    d[1] = llrint(ldexp(e[1], F));
+    d[0] = llrint(ldexp(ff_to(e.re), CQ_S));
+    d[1] = llrint(ldexp(ff_to(e.im), CQ_S));
   }
   if (threadIdx.x == 0 && j < nc - 1) {
-    const double r = R[((int64_t)j * nc + j) * 2];
-    const double v = r > 0.0 ? 1.0 / r : 0.0;
+    const double r = ff_to(cff_ld(R, (int64_t)j * nc + j).re);
+    const double v = r > 0.0 ? ldexp(1.0 / r, -((int)sexp[j] + CQ_S)) : 0.0;  // 1 / (r^_jj 2^(s_j + 62))
     int ex = 0;
     const double f = frexp(v, &ex);  // v = f 2^ex, f in [1/2, 1)
     ((long long *)Zs)[(size_t)j * 2] = llrint(ldexp(f, 62));
@@ -426,8 +498,9 @@ gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double
     const int nb = (nc + CQ_T - 1) / CQ_T;
     k_cq_gram<<<(unsigned)(nb * (nb + 1) / 2), CQ_THREADS, 0, st>>>(A, N, nc, sexp, R, status);
   }
+  k_cq_to_ff<<<(unsigned)nc, 128, 0, st>>>(R, nc, sexp, status);
   for (int p = 0; p < nc; p += CQ_T) {
-    k_cq_potrf<<<1, CQ_THREADS, 0, st>>>(R, nc, p, nrm0, n, status);
+    k_cq_potrf<<<1, CQ_THREADS, 0, st>>>(R, nc, p, nrm0, sexp, n, status);
     const int pe = p + CQ_T < nc ? p + CQ_T : nc;
     if (pe >= nc) break;
     const int cols = nc - pe;
