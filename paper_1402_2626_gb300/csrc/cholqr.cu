@@ -17,9 +17,10 @@
 // (bsb.cuh) once R is in their mantissa format.
 //
 // Accuracy: R from the Cholesky of the Gram matrix has a relative error of
-// about kappa(A)^2 u_double (against kappa u for MGS); the refinement only
-// needs the double factors to contract, which they do for kappa(A)^2 u << 1
-// (the mixed workload's Jacobian has kappa = 15).  Rank: a pivot below
+// about kappa(A)^2 u (against kappa u for MGS), u = 2^-47 for the
+// float-float Cholesky; the refinement only needs the factors to contract,
+// which they do for kappa(A)^2 u << 1 (the mixed workload's Jacobian has
+// kappa = 15).  Rank: a pivot below
 // 2^-40 of its column's squared norm (kappa above about 10^6, where the
 // double refinement would not converge) is reported as GN_ESINGULAR.
 #include "ifx.cuh"
