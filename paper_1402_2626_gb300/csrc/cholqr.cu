@@ -12,9 +12,9 @@
 // (gram_tc.cu, the columns rounded to 56 bits), else on the integer pipe
 // (k_cq_gram below, 62 bits), and only an O(n^3 / 3) Cholesky is left, in
 // float-float on the FP32 pipe (below).  The factor's last column is y = R^-H A^H b and R_nn = ||b - A x||,
-// as MGS on [A b] gives them (eq. 2), so the Gauss-Newton step and the
-// refinement's y = R^-H (A^H b) reuse the blocked integer triangular solves
-// (bsb.cuh) once R is in their mantissa format.
+// as MGS on [A b] gives them (eq. 2), so the Gauss-Newton step is R dx = y;
+// it and the refinement's R^H w = A^H b, R dx = w are blocked substitutions
+// with the float-float factor on one cluster (below).
 //
 // Accuracy: R from the Cholesky of the Gram matrix has a relative error of
 // about kappa(A)^2 u (against kappa u for MGS), u = 2^-47 for the
@@ -23,10 +23,17 @@
 // kappa = 15).  Rank: a pivot below
 // 2^-40 of its column's squared norm (kappa above about 10^6, where the
 // double refinement would not converge) is reported as GN_ESINGULAR.
+#include <cooperative_groups.h>
+
+#include <mutex>
+#include <type_traits>
+
 #include "ifx.cuh"
 #include "internal.h"
 
 namespace gn {
+
+namespace cg = cooperative_groups;
 
 constexpr int CQ_T = 32;        // tile width of the Gram matrix and of the Cholesky panels
 constexpr int CQ_THREADS = 256;
@@ -302,10 +309,15 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   __shared__ cff sB[CQ_T][CQ_T];           // [row][column]
   __shared__ unsigned short sPair[NPAIR];  // i << 8 | j
   __shared__ ffv sInv[CQ_T];
+  __shared__ float sThr[CQ_T];  // the rank test's pivot thresholds
   __shared__ int sBad;
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p);
   const int tid = threadIdx.x;
+  if (tid < pb) {
+    const float n0 = (float)ldexp(nrm0[p + tid], -((int)sexp[p + tid] + CQ_S));  // in (1/2, 1]
+    sThr[tid] = ldexpf(n0 * n0, -40);
+  }
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
     cff v = {{0.f, 0.f}, {0.f, 0.f}};
@@ -321,8 +333,7 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   // the pivot of row k (its thread only): r_kk, 1 / r_kk, the rank test
   auto pivot = [&](int k) {
     const ffv d = sB[k][k].re;
-    const float n0 = (float)ldexp(nrm0[p + k], -((int)sexp[p + k] + CQ_S));  // in (1/2, 1]
-    const bool bad = !(d.h > ldexpf(n0 * n0, -40));
+    const bool bad = !(d.h > sThr[k]);
     if (bad && p + k < nchk) {
       atomicCAS(status, GN_OK, GN_ESINGULAR);
       sBad = 1;
@@ -453,41 +464,377 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, 
     }
 }
 
-// R = R^ D (R^ in float-float, upper, leading dimension nc) into the
-// mantissa format of the integer triangular solves: column j's entries as
-// one-limb mantissas at 2^s_j (r_kj 2^-s_j = r^_kj 2^62, |r^_kj| <= 1), 1/r_jj
-// as a mantissa in [2^61, 2^62) and its exponent (Zs), 1/r_jj as a double
-// too.  One CTA per column.
-__global__ void k_cq_to_int(const double *__restrict__ R, int32_t nc, const double *__restrict__ sexp,
-                            double *__restrict__ Rm, double *__restrict__ Zs, double *__restrict__ rinv,
-                            const int32_t *__restrict__ status) {
+// ---- triangular solves with the float-float factor ----
+//
+// With R^ final, the Gauss-Newton step (R dx = y) and each refinement step
+// (R^H w = c, then R dx = w) are triangular solves needed to double accuracy
+// only: the refinement's corrections carry their own residual.  R = R^ D, so
+// R dx = y is R^ z = y^ with z = D dx, and R^H w = c is R^H w = D^-1 c.
+// Blocked substitution on one cluster of CQC CTAs: R^ is cut into CQB x CQB
+// diagonal blocks D_k whose inverses X_k = D_k^-1 are formed once per
+// factorisation (k_cq_binv); block b of the unknowns lives in CTA b mod CQC.
+// Per block, the owner of the next block brings that block's rows up to date
+// with the newest unknowns, forms the next CQB unknowns as X times its rows
+// and sends them to every CTA's shared memory; then every CTA updates its
+// other rows, and one cluster barrier ends the step.  The right-hand side is
+// scaled by a power of two first, its largest part in [1/2, 1), so the float
+// exponent range holds every intermediate value.
+
+constexpr int CQB = 32;                           // rows per block
+constexpr int CQC = 8;                            // CTAs of the cluster
+constexpr int CQC_THREADS = 512;
+constexpr int CQC_MAXN = 1024;                    // unknowns
+constexpr int CQC_OWN = CQC_MAXN / (CQB * CQC);   // blocks per CTA
+constexpr size_t CQC_SMEM =
+    sizeof(cff) * (CQC_OWN * CQB * CQB + 2 * CQC_OWN * CQB + 2 * CQB) + sizeof(double) * (CQC_THREADS / 32);
+
+// 1 / d for d > 0: the FP32 reciprocal and two Newton steps y += y (1 - d y)
+__device__ __forceinline__ ffv ff_recip(ffv d) {
+  ffv y = {__frcp_rn(d.h), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const ffv e = ff_add({1.f, 0.f}, ff_neg(ff_mul(d, y)));
+    y = ff_add(y, ff_mul(y, e));
+  }
+  return y;
+}
+
+// acc += a x, or conj(a) x
+template <bool CONJ>
+__device__ __forceinline__ void cff_mac(cff &acc, const cff &a, const cff &x) {
+  const ffv rr = ff_mul(a.re, x.re), ii = ff_mul(a.im, x.im);
+  const ffv ri = ff_mul(a.re, x.im), ir = ff_mul(a.im, x.re);
+  acc.re = ff_add(acc.re, CONJ ? ff_add(rr, ii) : ff_add(rr, ff_neg(ii)));
+  acc.im = ff_add(acc.im, CONJ ? ff_add(ri, ff_neg(ir)) : ff_add(ri, ir));
+}
+
+// the sum over the G lanes of an aligned lane group, in each of them
+template <int G>
+__device__ __forceinline__ cff cff_group_sum(cff v) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    cff u;
+    u.re.h = __shfl_xor_sync(0xffffffffu, v.re.h, o);
+    u.re.l = __shfl_xor_sync(0xffffffffu, v.re.l, o);
+    u.im.h = __shfl_xor_sync(0xffffffffu, v.im.h, o);
+    u.im.l = __shfl_xor_sync(0xffffffffu, v.im.l, o);
+    v.re = ff_add(v.re, u.re);
+    v.im = ff_add(v.im, u.im);
+  }
+  return v;
+}
+
+// X_k = D_k^-1 for the diagonal blocks of R^[0:n, 0:n] (upper), into the
+// strictly lower triangle of the same blocks: X_rc (r < c) at the place of
+// entry (b0 + c, b0 + r); X_rr = 1 / r_rr is formed where it is used.  One
+// CTA per block, warp c forming column c by substitution (lane i holding
+// row i: once x_l is known, rows i < l subtract d_il x_l and row l - 1 is
+// divided by its pivot).
+__global__ void __launch_bounds__(CQB * 32) k_cq_binv(double *__restrict__ R, int32_t nc, int32_t n,
+                                                     const int32_t *__restrict__ status) {
+  __shared__ cff sD[CQB][CQB + 1];  // [column][row]
   if (*status != GN_OK) return;
-  const int j = blockIdx.x;
-  for (int k = threadIdx.x; k <= j; k += blockDim.x) {
-    const cff e = cff_ld(R, (int64_t)j * nc + k);
-    long long *d = (long long *)(Rm + ((int64_t)j * nc + k) * 2);
-    d[0] = llrint(ldexp(ff_to(e.re), CQ_S));
-    d[1] = llrint(ldexp(ff_to(e.im), CQ_S));
+  const int b0 = blockIdx.x * CQB, bs = min(CQB, n - b0);
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  if (lane <= c && c < bs) sD[c][lane] = cff_ld(R, (int64_t)(b0 + c) * nc + b0 + lane);
+  __syncthreads();
+  if (c >= bs) return;  // whole warps, after the only barrier
+  ffv rinv = {0.f, 0.f};
+  if (lane < bs && sD[lane][lane].re.h > 0.f) rinv = ff_recip(sD[lane][lane].re);
+  cff x = {{0.f, 0.f}, {0.f, 0.f}};
+  if (lane == c) x.re = rinv;
+  for (int l = c; l >= 1; l--) {
+    cff xl;
+    xl.re.h = __shfl_sync(0xffffffffu, x.re.h, l);
+    xl.re.l = __shfl_sync(0xffffffffu, x.re.l, l);
+    xl.im.h = __shfl_sync(0xffffffffu, x.im.h, l);
+    xl.im.l = __shfl_sync(0xffffffffu, x.im.l, l);
+    if (lane < l) {
+      cff p = {{0.f, 0.f}, {0.f, 0.f}};
+      cff_mac<false>(p, sD[l][lane], xl);
+      x.re = ff_add(x.re, ff_neg(p.re));
+      x.im = ff_add(x.im, ff_neg(p.im));
+      if (lane == l - 1) x = cff_scale(x, rinv);
+    }
   }
-  if (threadIdx.x == 0 && j < nc - 1) {
-    const double r = ff_to(cff_ld(R, (int64_t)j * nc + j).re);
-    const double v = r > 0.0 ? ldexp(1.0 / r, -((int)sexp[j] + CQ_S)) : 0.0;  // 1 / (r^_jj 2^(s_j + 62))
-    int ex = 0;
-    const double f = frexp(v, &ex);  // v = f 2^ex, f in [1/2, 1)
-    ((long long *)Zs)[(size_t)j * 2] = llrint(ldexp(f, 62));
-    Zs[(size_t)j * 2 + 1] = (double)(ex - 62);
-    rinv[j] = v;
+  if (lane < c) cff_st(R, (int64_t)(b0 + lane) * nc + b0 + c, x);
+}
+
+// REFINE: R^H w = c, then R dx = w for c (double complex [n]); else R dx = y
+// with y the factor's last column.  R^ in float-float (leading dimension
+// nc = n + 1) with the block inverses of k_cq_binv; dx double complex [n].
+template <bool REFINE>
+__global__ void __launch_bounds__(CQC_THREADS, 1) k_cq_solve(const double *__restrict__ R, int32_t nc, int32_t n,
+                                                             const double *__restrict__ sexp,
+                                                             const double *__restrict__ c,
+                                                             double *__restrict__ dx,
+                                                             int32_t *__restrict__ status) {
+  extern __shared__ __align__(16) float4 cq_sm[];
+  cff *sXb = (cff *)cq_sm;              // [CQC_OWN][CQB][CQB] X of this CTA's blocks, [row][column]
+  cff *sY = sXb + CQC_OWN * CQB * CQB;  // [CQC_OWN * CQB] the rows of this CTA's blocks
+  cff *sU = sY + CQC_OWN * CQB;         // [CQC_OWN * CQB] the unknowns of this CTA's blocks
+  cff *sX = sU + CQC_OWN * CQB;         // [2][CQB] the newest block of unknowns
+  double *smax = (double *)(sX + 2 * CQB);
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const bool run = *status == GN_OK;  // the same in every CTA: nothing writes it before the end
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nb = (n + CQB - 1) / CQB;
+  auto bsz = [&](int b) { return min(CQB, n - b * CQB); };
+  auto rhs = [&](int i, double &vr, double &vi) {
+    if (REFINE) {
+      const int sc = -((int)sexp[i] + CQ_S);
+      vr = ldexp(c[2 * i], sc);
+      vi = ldexp(c[2 * i + 1], sc);
+    } else {
+      const cff y = cff_ld(R, (int64_t)n * nc + i);
+      vr = ff_to(y.re);
+      vi = ff_to(y.im);
+    }
+  };
+  // the scale: every CTA forms max |v| over all n rows (the same value)
+  double m = 0.0;
+  if (run)
+    for (int i = tid; i < n; i += CQC_THREADS) {
+      double vr, vi;
+      rhs(i, vr, vi);
+      m = fmax(m, (isfinite(vr) && isfinite(vi)) ? fmax(fabs(vr), fabs(vi)) : HUGE_VAL);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0) smax[warp] = m;
+  __syncthreads();
+  m = lane < CQC_THREADS / 32 ? smax[lane] : 0.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const bool go = run && isfinite(m);  // uniform over the cluster
+  if (run && !go && rank == 0 && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
+  int e = 0;
+  if (go && m > 0.0) frexp(m, &e);  // max |v| < 2^e
+  const int nown = rank < nb ? (nb - 1 - rank) / CQC + 1 : 0;
+  if (go) {
+    for (int q = 0; q < nown; q++) {
+      const int b = rank + CQC * q, b0 = b * CQB, bs = bsz(b);
+      for (int r = tid; r < bs; r += CQC_THREADS) {
+        double vr, vi;
+        rhs(b0 + r, vr, vi);
+        sY[q * CQB + r] = {ff_from(ldexp(vr, -e)), ff_from(ldexp(vi, -e))};
+      }
+      for (int idx = tid; idx < CQB * CQB; idx += CQC_THREADS) {
+        const int r = idx / CQB, cc = idx % CQB;
+        cff v = {{0.f, 0.f}, {0.f, 0.f}};
+        if (r < bs && cc < bs) {
+          if (r < cc) {
+            v = cff_ld(R, (int64_t)(b0 + r) * nc + b0 + cc);
+          } else if (r == cc) {
+            const ffv d = cff_ld(R, (int64_t)(b0 + r) * nc + b0 + r).re;
+            if (d.h > 0.f) v.re = ff_recip(d);
+          }
+        }
+        sXb[(q * CQB + r) * CQB + cc] = v;
+      }
+    }
   }
+  __syncthreads();
+  cl.sync();  // rows loaded; every CTA started (the stores below may target it)
+
+  // Rows of the owned blocks of slots [q0, q1) minus the product of block
+  // column k (forward: conj(R^(k, rows))^T) with the unknowns in buffer buf,
+  // G lanes per row, all rows in one pass.  The entries of R^ are loaded a
+  // step ahead (load), before the cluster barrier, so the update waits for
+  // no load.
+  auto load = [&](auto gtag, bool fwd, int k, int q0, int q1, cff *ent) {
+    constexpr int G = decltype(gtag)::value;
+    const int k0 = k * CQB, kb = bsz(k), p = tid % G;
+    const int s = q0 * CQB + tid / G, q = s / CQB, r = s % CQB;
+    const int b = rank + CQC * q, i = b * CQB + r;
+    const bool act = s < q1 * CQB && r < bsz(b);
+#pragma unroll
+    for (int t = 0; t < CQB / G; t++) {
+      const int cc = p + G * t;
+      ent[t] = {{0.f, 0.f}, {0.f, 0.f}};
+      if (act && cc < kb)
+        ent[t] = fwd ? cff_ld(R, (int64_t)i * nc + k0 + cc) : cff_ld(R, (int64_t)(k0 + cc) * nc + i);
+    }
+  };
+  auto update = [&](auto gtag, bool fwd, int k, int buf, int q0, int q1, const cff *ent) {
+    constexpr int G = decltype(gtag)::value;
+    const int kb = bsz(k), p = tid % G;
+    const int s = q0 * CQB + tid / G, q = s / CQB, r = s % CQB;
+    const bool act = s < q1 * CQB && r < bsz(rank + CQC * q);
+    cff acc[2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};  // two chains
+#pragma unroll
+    for (int t = 0; t < CQB / G; t++) {
+      const int cc = p + G * t;
+      if (act && cc < kb) {
+        if (fwd) {
+          cff_mac<true>(acc[t & 1], ent[t], sX[buf * CQB + cc]);
+        } else {
+          cff_mac<false>(acc[t & 1], ent[t], sX[buf * CQB + cc]);
+        }
+      }
+    }
+    acc[0].re = ff_add(acc[0].re, acc[1].re);
+    acc[0].im = ff_add(acc[0].im, acc[1].im);
+    const cff sum = cff_group_sum<G>(acc[0]);
+    if (act && p == 0) {
+      cff y = sY[s];
+      y.re = ff_add(y.re, ff_neg(sum.re));
+      y.im = ff_add(y.im, ff_neg(sum.im));
+      sY[s] = y;
+    }
+  };
+  // the unknowns of owned block k (slot q) from its rows: X_k y (backward) or
+  // X_k^H g (forward), 16 lanes per row; lane t < CQC of a row sends it to
+  // buffer buf of CTA t, and it is kept in sU
+  auto xstep = [&](bool fwd, int k, int buf) {
+    constexpr int G = CQC_THREADS / CQB;
+    static_assert(CQC < G, "a lane of the row's group for each CTA");
+    const int q = (k - rank) / CQC, kb = bsz(k);
+    const int r = tid / G, p = tid % G;
+    cff acc = {{0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int t = 0; t < CQB / G; t++) {
+      const int cc = p + G * t;
+      if (cc < kb) {
+        if (fwd) {
+          if (cc <= r) cff_mac<true>(acc, sXb[(q * CQB + cc) * CQB + r], sY[q * CQB + cc]);
+        } else {
+          if (cc >= r) cff_mac<false>(acc, sXb[(q * CQB + r) * CQB + cc], sY[q * CQB + cc]);
+        }
+      }
+    }
+    acc = cff_group_sum<G>(acc);
+    if (r < kb) {
+      const float4 v = make_float4(acc.re.h, acc.re.l, acc.im.h, acc.im.l);
+      if (p < CQC) *((float4 *)cl.map_shared_rank(sX, p) + buf * CQB + r) = v;
+      if (p == CQC) *((float4 *)sU + q * CQB + r) = v;
+    }
+  };
+  using G4 = std::integral_constant<int, 4>;
+  using G16 = std::integral_constant<int, CQC_THREADS / CQB>;
+  static_assert(CQC_OWN * CQB * 4 <= CQC_THREADS, "the other rows in one pass of 4 lanes each");
+  // the owned slots of blocks in [lo, hi)
+  auto slot_lo = [&](int lo) { return lo <= rank ? 0 : (lo - rank + CQC - 1) / CQC; };
+  auto slot_hi = [&](int hi) { return hi <= rank ? 0 : min(nown, (hi - rank + CQC - 1) / CQC); };
+  auto slot_of = [&](int b) { return (b - rank) / CQC; };  // b owned
+  // the entries of the next steps: e16 for this CTA's next turn as owner
+  // (loaded right after its previous turn, CQC steps ahead), e4 for the
+  // other rows of the next step
+  cff e16[CQB / 16], e4[CQB / 4];
+  if (REFINE) {
+    // forward: w_k = X_k^H (g_k - sum_{j<k} R_jk^H w_j), blocks in order; step
+    // k applies w_k to block k+1 (its owner first) and to the blocks after it
+    auto owns = [&](int k) { return rank == (k + 1) % CQC; };
+    auto fetch16 = [&](int k) { load(G16{}, true, k, slot_of(k + 1), slot_of(k + 1) + 1, e16); };
+    auto fetch4 = [&](int k) { load(G4{}, true, k, slot_lo(k + 2), slot_hi(nb), e4); };
+    if (go && nb > 1) {
+      for (int k = 0; k + 1 < nb && k < CQC; k++)
+        if (owns(k)) fetch16(k);
+      fetch4(0);
+    }
+    if (go && rank == 0) xstep(true, 0, 0);
+    cl.sync();
+    for (int k = 0; k + 1 < nb; k++) {
+      const int buf = k & 1;
+      if (go) {
+        if (owns(k)) {
+          const int q = slot_of(k + 1);
+          update(G16{}, true, k, buf, q, q + 1, e16);  // block k+1 first
+          if (k + CQC + 1 < nb) fetch16(k + CQC);
+          __syncthreads();
+          xstep(true, k + 1, buf ^ 1);
+        }
+        update(G4{}, true, k, buf, slot_lo(k + 2), slot_hi(nb), e4);  // the other owned blocks below
+        if (k + 2 < nb) fetch4(k + 1);
+      }
+      cl.sync();
+    }
+  }
+  if (REFINE) {  // w is the backward solve's right-hand side
+    for (int t = tid; t < nown * CQB; t += CQC_THREADS) sY[t] = sU[t];
+    __syncthreads();
+  }
+  // backward: x_k = X_k (y_k - sum_{j>k} R_kj x_j), blocks from the last;
+  // step k applies x_k to block k-1 (its owner first) and to the blocks above
+  auto owns = [&](int k) { return rank == (k - 1) % CQC; };
+  auto fetch16 = [&](int k) { load(G16{}, false, k, slot_of(k - 1), slot_of(k - 1) + 1, e16); };
+  auto fetch4 = [&](int k) { load(G4{}, false, k, 0, slot_hi(k - 1), e4); };
+  if (go && nb > 1) {
+    for (int k = nb - 1; k >= 1 && k > nb - 1 - CQC; k--)
+      if (owns(k)) fetch16(k);
+    fetch4(nb - 1);
+  }
+  if (go && rank == (nb - 1) % CQC) xstep(false, nb - 1, (nb - 1) & 1);
+  cl.sync();
+  for (int k = nb - 1; k >= 1; k--) {
+    const int buf = k & 1;
+    if (go) {
+      if (owns(k)) {
+        const int q = slot_of(k - 1);
+        update(G16{}, false, k, buf, q, q + 1, e16);  // block k-1 first
+        if (k - CQC >= 1) fetch16(k - CQC);
+        __syncthreads();
+        xstep(false, k - 1, buf ^ 1);
+      }
+      update(G4{}, false, k, buf, 0, slot_hi(k - 1), e4);  // the other owned blocks above
+      if (k - 1 >= 1) fetch4(k - 1);
+    }
+    cl.sync();
+  }
+  // dx of the owned rows: REFINE dx = D^-1 z, else dx = D^-1 z 2^(s_n + 62);
+  // and the scale 2^e back
+  if (go)
+    for (int t = tid; t < nown * CQB; t += CQC_THREADS) {
+      const int b = rank + CQC * (t / CQB), r = t % CQB, i = b * CQB + r;
+      if (r >= bsz(b)) continue;
+      const int sh = REFINE ? e - ((int)sexp[i] + CQ_S) : e + (int)sexp[n] - (int)sexp[i];
+      const double xr = ldexp(ff_to(sU[t].re), sh), xi = ldexp(ff_to(sU[t].im), sh);
+      if (!isfinite(xr) || !isfinite(xi)) atomicCAS(status, GN_OK, GN_ENONFINITE);
+      dx[2 * i] = xr;
+      dx[2 * i + 1] = xi;
+    }
+}
+
+gn_status launch_cq_solve(bool refine, int32_t n, const double *R, const double *sexp, const double *c,
+                          double *dx, int32_t *status, cudaStream_t st) {
+  if (n < 1 || n > CQC_MAXN) return GN_EINVAL;
+  static std::mutex mu;
+  static int ready = -1;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    if (ready < 0)
+      ready = cudaFuncSetAttribute(k_cq_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)CQC_SMEM) == cudaSuccess &&
+              cudaFuncSetAttribute(k_cq_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)CQC_SMEM) == cudaSuccess;
+  }
+  if (!ready) return GN_ECUDA;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(CQC);
+  cfg.blockDim = dim3(CQC_THREADS);
+  cfg.dynamicSmemBytes = CQC_SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeClusterDimension;
+  attr.val.clusterDim.x = CQC;
+  attr.val.clusterDim.y = 1;
+  attr.val.clusterDim.z = 1;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  const int32_t nc = n + 1;
+  const cudaError_t err = refine ? cudaLaunchKernelEx(&cfg, k_cq_solve<true>, R, nc, n, sexp, c, dx, status)
+                                 : cudaLaunchKernelEx(&cfg, k_cq_solve<false>, R, nc, n, sexp, c, dx, status);
+  return err == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 
 bool cholqr_available(const gn_system *s) {
-  // the blocked integer solves it hands R to take 32 .. 1024 unknowns
-  return s->arith != GN_ARITH_FP64 && s->n >= 32 && s->n <= BACKSUB_INT_MAX_N && s->N >= s->n &&
-         fwdsub_int_available(1, s->n);
+  // the cluster solves hold at most CQC_MAXN unknowns: 32 .. 1024
+  return s->arith != GN_ARITH_FP64 && s->n >= 32 && s->n <= CQC_MAXN && s->N >= s->n;
 }
 
-gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, double *Rm,
-                        double *Zs, void *scratch, int32_t *status, cudaStream_t st) {
+gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, void *scratch,
+                        int32_t *status, cudaStream_t st) {
   const int32_t nc = n + 1;
   double *nrm0 = rinv + nc, *sexp = rinv + 2 * (size_t)nc;  // the layout of the one-limb rinv
   k_cq_scale<<<(unsigned)((nc * 32 + CQ_THREADS - 1) / CQ_THREADS), CQ_THREADS, 0, st>>>(A, N, nc, nrm0,
@@ -510,7 +857,7 @@ gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double
     const int tb = (cols + CQ_T - 1) / CQ_T;
     k_cq_herk<<<(unsigned)(tb * (tb + 1) / 2), CQ_THREADS, 0, st>>>(R, nc, p, status);
   }
-  k_cq_to_int<<<(unsigned)nc, 128, 0, st>>>(R, nc, sexp, Rm, Zs, rinv, status);
+  k_cq_binv<<<(unsigned)((n + CQB - 1) / CQB), CQB * 32, 0, st>>>(R, nc, n, status);
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;
 }
 

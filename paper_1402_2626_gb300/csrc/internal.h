@@ -159,11 +159,19 @@ inline size_t bs_inv_doubles(int32_t n, int L) {
 }
 constexpr int BACKSUB_INT_MAX_N = 1024;
 // CholeskyQR of [A b] (double complex, N x (n+1), leading dimension N) for the
-// mixed solver: R (double, upper, leading dimension n+1) and its mantissa
-// form (Rm, Zs, the column exponents in rinv) for the integer solves
+// mixed solver: R^ (float-float in the double-complex slots of R, upper,
+// leading dimension n+1; the inverses of its 32 x 32 diagonal blocks below
+// the diagonal), with R = R^ D,
+// D = diag(2^(s_j + 62)); the column norms and exponents s_j at rinv + n+1 and
+// rinv + 2(n+1)
 bool cholqr_available(const gn_system *s);
-gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, double *Rm,
-                        double *Zs, void *scratch, int32_t *status, cudaStream_t st);
+gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, void *scratch,
+                        int32_t *status, cudaStream_t st);
+// Solves with that factor, dx double complex [n]: R dx = y (y = the factor's
+// last column; refine = false), or R^H w = c then R dx = w (refine = true, c
+// double complex [n]); sexp = rinv + 2(n+1)
+gn_status launch_cq_solve(bool refine, int32_t n, const double *R, const double *sexp, const double *c,
+                          double *dx, int32_t *status, cudaStream_t st);
 // The Gram matrix G = A^H A (upper triangle, double complex, leading
 // dimension nc) of A (N x nc, leading dimension N) on the tensor cores,
 // exact for the columns rounded to 56 bits at their scales 2^sexp_j;

@@ -24,7 +24,8 @@
 // (whose last column is y = R^-H J^H (-f)), R dx = y and x += dx; each
 // refinement forms c = J^H b with the frozen J, R^H w = c, then R dx = w
 // (the normal equations through the Cholesky factor, kappa(J)^2 u_double
-// per step, which the refinement tolerates for kappa(J)^2 u << 1).
+// per step, which the refinement tolerates for kappa(J)^2 u << 1).  Both
+// solves run on the float-float factor itself, on one cluster (cholqr.cu).
 #include <string.h>
 
 #include "internal.h"
@@ -199,22 +200,20 @@ static gn_status refine_step(gn_system *s, Workspace *w1, Workspace *wL, double 
 
 // One refinement step with the frozen CholeskyQR factors of the last double
 // step (cholqr.cu): b = -f(x) at precision L, c = J^H b, R^H w = c, R dx = w
-// (both blocked solves on the factor's mantissas), x += dx at precision L.
+// (both substitutions in one launch on the float-float factor), x += dx at
+// precision L.
 template <int L>
 static gn_status refine_step_cq(gn_system *s, Workspace *w1, Workspace *wL, double *d_x, cudaStream_t st) {
   const int32_t N = s->N, n = s->n;
   const int64_t W = 2 * L;
   double *negf = wL->Ab + (int64_t)n * N * W;
   double *fnorm = wL->rinv;
-  double *c = w1->lam, *w = wL->lam;  // [n] double complex each (lam holds N >= n entries)
-  double *sexp = w1->rinv + 2 * (size_t)(n + 1);
+  double *c = w1->lam;  // [n] double complex (lam holds N >= n entries)
+  const double *sexp = w1->rinv + 2 * (size_t)(n + 1);
   gn_status e = launch_eval_sel(s, L, d_x, negf, 1, nullptr, N, st);
   if (e) return e;
   k_mix_ahb<L><<<(unsigned)n, MIX_THREADS, 0, st>>>(w1->Ab, N, N, negf, c, fnorm, wL->status);
-  e = launch_fwdsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, c, w, wL->status, st);
-  if (e) return e;
-  k_mix_y_fixed<<<1, MIX_THREADS, 0, st>>>(w, w1->Rm, n + 1, n, sexp, wL->status);
-  e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, wL->status, st);
+  e = launch_cq_solve(true, n, w1->R, sexp, c, w1->dx, wL->status, st);
   if (e) return e;
   k_mix_spread<L><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(n, w1->dx, wL->dx);
   return launch_update(L, n, d_x, wL->dx, fnorm, wL->norms, wL->status, st);
@@ -244,9 +243,8 @@ static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_r
   }
   for (int32_t k = 0; k < d_steps; k++) {
     gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, st);
-    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->Rm, w1->Zs, w1->cq_scratch, w1->status, st);
-    if (!e)
-      e = launch_backsub_int(1, w1->Rm, n + 1, n, w1->Zs, w1->rinv, w1->Xinv, w1->dx, w1->status, st);
+    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->cq_scratch, w1->status, st);
+    if (!e) e = launch_cq_solve(false, n, w1->R, w1->rinv + 2 * (size_t)(n + 1), nullptr, w1->dx, w1->status, st);
     if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, st);
     if (e) return e;
   }
