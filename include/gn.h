@@ -196,7 +196,8 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  * factorisation is CholeskyQR: R from the Cholesky factor of the Gram
  * matrix of [J, -f] (scaled by its columns' powers of two, in float-float
  * arithmetic on the FP32 pipe: about 47 significant bits), Q never formed,
- * and the refinement's y = R^-H (J^H b); its error, about kappa(J)^2 2^-47,
+ * and the refinement's y = R^-H (J^H b); the triangular solves run on the
+ * float-float factor too (blocked, on one 8-CTA cluster); its error, about kappa(J)^2 2^-47,
  * suits Jacobians with kappa(J)^2 2^-47 << 1, and a pivot below 2^-20 of its
  * column's norm is reported as GN_ESINGULAR.  The Gram matrix is exact for the columns
  * rounded at their scales, then rounded once to doubles: on the tensor
