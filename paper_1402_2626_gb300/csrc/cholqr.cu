@@ -416,15 +416,25 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, 
 // The trailing matrix: G^_ij -= sum_{k in the panel} conj(r_ki) r_kj for
 // pe <= i <= j < nc, by 32 x 32 tiles (ib <= jb over the trailing range), 256
 // threads of 2 x 2 entries, the panel's rows of both tiles' columns staged
-// in shared memory.
+// in shared memory.  part 0: every tile; 1: the tiles of the next panel's
+// rows (ib = 0, one CTA per jb); 2: the others (ib >= 1).
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, int32_t nc, int32_t p,
-                                                        const int32_t *__restrict__ status) {
+                                                        int32_t part, const int32_t *__restrict__ status) {
   __shared__ cff sI[CQ_T][CQ_T];  // [panel row][column of the i tile]
   __shared__ cff sJ[CQ_T][CQ_T];
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p), pe = p + pb;
   int ib, jb;
-  cq_tile(blockIdx.x, ib, jb);
+  if (part == 1) {  // the next panel's rows only
+    ib = 0;
+    jb = blockIdx.x;
+  } else {
+    cq_tile(blockIdx.x, ib, jb);
+    if (part == 2) {  // every tile below them
+      ib++;
+      jb++;
+    }
+  }
   const int i0 = pe + ib * CQ_T, j0 = pe + jb * CQ_T;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
@@ -833,8 +843,16 @@ bool cholqr_available(const gn_system *s) {
   return s->arith != GN_ARITH_FP64 && s->n >= 32 && s->n <= CQC_MAXN && s->N >= s->n;
 }
 
+// With a second stream (side, created at the highest priority) and two
+// events the panels look one ahead: the panels' Cholesky, row block and the
+// trailing update of the next panel's rows run on side, so the next panel
+// follows at once, while the rest of each trailing update runs on st; the
+// next panel's own trailing update waits for that rest (it updates the same
+// rows).  The priority gives the panels' launches the SMs that free up
+// while a large trailing update fills the GPU.
 gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, void *scratch,
-                        int32_t *status, cudaStream_t st) {
+                        int32_t *status, cudaStream_t st, cudaStream_t side, cudaEvent_t ev_panel,
+                        cudaEvent_t ev_trail) {
   const int32_t nc = n + 1;
   double *nrm0 = rinv + nc, *sexp = rinv + 2 * (size_t)nc;  // the layout of the one-limb rinv
   k_cq_scale<<<(unsigned)((nc * 32 + CQ_THREADS - 1) / CQ_THREADS), CQ_THREADS, 0, st>>>(A, N, nc, nrm0,
@@ -847,15 +865,40 @@ gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double
     k_cq_gram<<<(unsigned)(nb * (nb + 1) / 2), CQ_THREADS, 0, st>>>(A, N, nc, sexp, R, status);
   }
   k_cq_to_ff<<<(unsigned)nc, 128, 0, st>>>(R, nc, sexp, status);
+  const bool ahead = side && ev_panel && ev_trail;
+  cudaStream_t ps = st;  // the panels' stream
+  if (ahead) {
+    ps = side;
+    if (cudaEventRecord(ev_trail, st) != cudaSuccess || cudaStreamWaitEvent(ps, ev_trail, 0) != cudaSuccess)
+      return GN_ECUDA;
+  }
+  bool trail = false;  // a trailing update is in flight on st
   for (int p = 0; p < nc; p += CQ_T) {
-    k_cq_potrf<<<1, CQ_THREADS, 0, st>>>(R, nc, p, nrm0, sexp, n, status);
+    k_cq_potrf<<<1, CQ_THREADS, 0, ps>>>(R, nc, p, nrm0, sexp, n, status);
     const int pe = p + CQ_T < nc ? p + CQ_T : nc;
     if (pe >= nc) break;
     const int cols = nc - pe;
-    k_cq_trsm<<<(unsigned)((cols + CQ_THREADS / 32 - 1) / (CQ_THREADS / 32)), CQ_THREADS, 0, st>>>(R, nc, p,
+    k_cq_trsm<<<(unsigned)((cols + CQ_THREADS / 32 - 1) / (CQ_THREADS / 32)), CQ_THREADS, 0, ps>>>(R, nc, p,
                                                                                                 status);
     const int tb = (cols + CQ_T - 1) / CQ_T;
-    k_cq_herk<<<(unsigned)(tb * (tb + 1) / 2), CQ_THREADS, 0, st>>>(R, nc, p, status);
+    if (!ahead) {
+      k_cq_herk<<<(unsigned)(tb * (tb + 1) / 2), CQ_THREADS, 0, st>>>(R, nc, p, 0, status);
+      continue;
+    }
+    if (cudaEventRecord(ev_panel, ps) != cudaSuccess) return GN_ECUDA;  // the row block is done
+    // the next panel's rows: after the previous rest, which updated them too
+    if (trail && cudaStreamWaitEvent(ps, ev_trail, 0) != cudaSuccess) return GN_ECUDA;
+    k_cq_herk<<<(unsigned)tb, CQ_THREADS, 0, ps>>>(R, nc, p, 1, status);
+    trail = tb > 1;
+    if (trail) {
+      if (cudaStreamWaitEvent(st, ev_panel, 0) != cudaSuccess) return GN_ECUDA;
+      k_cq_herk<<<(unsigned)((tb - 1) * tb / 2), CQ_THREADS, 0, st>>>(R, nc, p, 2, status);
+      if (cudaEventRecord(ev_trail, st) != cudaSuccess) return GN_ECUDA;
+    }
+  }
+  if (ahead) {  // st continues after the last panel (its own rests are in order)
+    if (cudaEventRecord(ev_panel, ps) != cudaSuccess || cudaStreamWaitEvent(st, ev_panel, 0) != cudaSuccess)
+      return GN_ECUDA;
   }
   k_cq_binv<<<(unsigned)((n + CQB - 1) / CQB), CQB * 32, 0, st>>>(R, nc, n, status);
   return cudaPeekAtLastError() == cudaSuccess ? GN_OK : GN_ECUDA;

@@ -51,6 +51,9 @@ static void ws_free(Workspace &w) {
   cudaFree(w.Zs);
   cudaFree(w.Xinv);
   cudaFree(w.cq_scratch);
+  if (w.cq_ev[0]) cudaEventDestroy(w.cq_ev[0]);
+  if (w.cq_ev[1]) cudaEventDestroy(w.cq_ev[1]);
+  if (w.cq_side) cudaStreamDestroy(w.cq_side);
   if (w.h_norms) cudaFreeHost(w.h_norms);
   if (w.h_status) cudaFreeHost(w.h_status);
   w = Workspace();

@@ -40,6 +40,8 @@ struct Workspace {
   double *Xinv = nullptr;       // inverses of R's 16 x 16 diagonal blocks (blocked back substitution)
   void *cq_scratch = nullptr;   // CholeskyQR's tensor-core Gram scratch (allocated on first use)
   size_t cq_bytes = 0;
+  cudaStream_t cq_side = nullptr;          // CholeskyQR's lookahead: the panels' stream
+  cudaEvent_t cq_ev[2] = {nullptr, nullptr};  // and its two events (created on first use)
   double *h_norms = nullptr;    // pinned host copy of norms
   int32_t *h_status = nullptr;  // pinned host copy of status
   // what Ab, R, Rm, Zs and rinv hold: 0 nothing reusable; 1 / 2 the
@@ -166,7 +168,8 @@ constexpr int BACKSUB_INT_MAX_N = 1024;
 // rinv + 2(n+1)
 bool cholqr_available(const gn_system *s);
 gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double *rinv, void *scratch,
-                        int32_t *status, cudaStream_t st);
+                        int32_t *status, cudaStream_t st, cudaStream_t side = nullptr,
+                        cudaEvent_t ev_panel = nullptr, cudaEvent_t ev_trail = nullptr);
 // Solves with that factor, dx double complex [n]: R dx = y (y = the factor's
 // last column; refine = false), or R^H w = c then R dx = w (refine = true, c
 // double complex [n]); sexp = rinv + 2(n+1)

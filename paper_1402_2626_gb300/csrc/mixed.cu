@@ -241,9 +241,30 @@ static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_r
       w1->cq_scratch = nullptr;
     }
   }
+  // the Cholesky's lookahead stream (at the highest priority) and events,
+  // kept with the workspace; without them the panels run on st alone
+  if (!w1->cq_side) {
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, hi) == cudaSuccess &&
+        cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess) {
+      w1->cq_side = side;
+      w1->cq_ev[0] = ev[0];
+      w1->cq_ev[1] = ev[1];
+    } else {
+      if (ev[0]) cudaEventDestroy(ev[0]);
+      if (side) cudaStreamDestroy(side);
+      cudaGetLastError();
+    }
+  }
   for (int32_t k = 0; k < d_steps; k++) {
     gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, st);
-    if (!e) e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->cq_scratch, w1->status, st);
+    if (!e)
+      e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->cq_scratch, w1->status, st, w1->cq_side,
+                        w1->cq_ev[0], w1->cq_ev[1]);
     if (!e) e = launch_cq_solve(false, n, w1->R, w1->rinv + 2 * (size_t)(n + 1), nullptr, w1->dx, w1->status, st);
     if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, st);
     if (e) return e;
