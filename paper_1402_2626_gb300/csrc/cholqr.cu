@@ -255,6 +255,17 @@ __device__ __forceinline__ ffv ff_rsqrt(ffv d) {
   return y;
 }
 
+// 1 / d for d > 0: the FP32 reciprocal and two Newton steps y += y (1 - d y)
+__device__ __forceinline__ ffv ff_recip(ffv d) {
+  ffv y = {__frcp_rn(d.h), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; it++) {
+    const ffv e = ff_add({1.f, 0.f}, ff_neg(ff_mul(d, y)));
+    y = ff_add(y, ff_mul(y, e));
+  }
+  return y;
+}
+
 // g -= conj(a) b
 __device__ __forceinline__ void cff_sub_conj_mul(cff &g, const cff &a, const cff &b) {
   const ffv re = ff_add(ff_mul(a.re, b.re), ff_mul(a.im, b.im));
@@ -292,14 +303,16 @@ __global__ void k_cq_to_ff(double *__restrict__ G, int32_t nc, const double *__r
 }
 
 // The panel's diagonal block G^[p:pe, p:pe] = R11^H R11 (upper, in place)
-// by one CTA in shared memory, right-looking: after row k is final (r_kk =
-// sqrt(g_kk), the rest of the row times 1 / r_kk), every g_ij with
-// k < i <= j less conj(r_ki) r_kj.  The pairs (i, j), 1 <= i <= j < 32, are
-// listed by decreasing i, so the pairs still to update after row k are the
-// first (31 - k)(32 - k) / 2 of the list and a step's threads are packed
-// into whole warps.  The thread of pair (k + 1, k + 1) takes the next pivot
-// as soon as it has updated it.  A pivot g_kk <= 2^-40 ||a_k||^2 (k < nchk;
-// in the scaled units) records GN_ESINGULAR.
+// by one CTA in shared memory, right-looking on the unscaled rows: with
+// pivot d_k = g_kk final, every g_ij with k < i <= j less conj(g_ki) g_kj / d_k
+// (= conj(r_ki) r_kj), so a step needs the reciprocal of its pivot only; the
+// square roots and the rows' scaling, r_kj = g_kj / sqrt(d_k), follow for all
+// rows at once at the end.  The pairs (i, j), 1 <= i <= j < 32, are listed by
+// decreasing i, so the pairs still to update after row k are the first
+// (31 - k)(32 - k) / 2 of the list and a step's threads are packed into whole
+// warps.  The thread of pair (k + 1, k + 1) takes the next pivot as soon as
+// it has updated it: one barrier per step.  A pivot d_k <= 2^-40 ||a_k||^2
+// (k < nchk; in the scaled units) records GN_ESINGULAR.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G, int32_t nc, int32_t p,
                                                          const double *__restrict__ nrm0,
                                                          const double *__restrict__ sexp, int32_t nchk,
@@ -308,8 +321,8 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   static_assert(NPAIR <= 2 * CQ_THREADS, "two pairs per thread");
   __shared__ cff sB[CQ_T][CQ_T];           // [row][column]
   __shared__ unsigned short sPair[NPAIR];  // i << 8 | j
-  __shared__ ffv sInv[CQ_T];
-  __shared__ float sThr[CQ_T];  // the rank test's pivot thresholds
+  __shared__ ffv sInv[CQ_T];               // 1 / d_k, then 1 / sqrt(d_k)
+  __shared__ float sThr[CQ_T];             // the rank test's pivot thresholds
   __shared__ int sBad;
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p);
@@ -330,7 +343,7 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
   }
   if (tid == 0) sBad = 0;
   __syncthreads();
-  // the pivot of row k (its thread only): r_kk, 1 / r_kk, the rank test
+  // the pivot d_k (its thread only): the rank test and 1 / d_k
   auto pivot = [&](int k) {
     const ffv d = sB[k][k].re;
     const bool bad = !(d.h > sThr[k]);
@@ -338,18 +351,13 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
       atomicCAS(status, GN_OK, GN_ESINGULAR);
       sBad = 1;
     }
-    const ffv inv = d.h > 0.f ? ff_rsqrt(d) : ffv{0.f, 0.f};
-    sB[k][k] = {ff_mul(d, inv), {0.f, 0.f}};
-    sInv[k] = inv;
+    sInv[k] = d.h > 0.f ? ff_recip(d) : ffv{0.f, 0.f};
   };
   if (tid == 0) pivot(0);
-  for (int k = 0;; k++) {
+  for (int k = 0; k + 1 < pb; k++) {
     __syncthreads();
     if (sBad) return;  // uniform: read after the barrier
     const ffv inv = sInv[k];
-    for (int j = k + 1 + tid; j < CQ_T; j += CQ_THREADS) sB[k][j] = cff_scale(sB[k][j], inv);
-    if (k + 1 >= pb) break;
-    __syncthreads();
     const int np = (CQ_T - 1 - k) * (CQ_T - k) / 2, qk = (CQ_T - 2 - k) * (CQ_T - 1 - k) / 2;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -357,16 +365,26 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_potrf(double *__restrict__ G,
       if (q < np) {
         const int pr = sPair[q], i = pr >> 8, j = pr & 255;
         cff g = sB[i][j];
-        cff_sub_conj_mul(g, sB[k][i], sB[k][j]);
+        cff_sub_conj_mul(g, sB[k][i], cff_scale(sB[k][j], inv));
         sB[i][j] = g;
         if (q == qk) pivot(k + 1);  // pair (k + 1, k + 1)
       }
     }
   }
   __syncthreads();
+  if (sBad) return;
+  if (tid < pb) {  // 1 / sqrt(d_k)
+    const ffv d = sB[tid][tid].re;
+    sInv[tid] = d.h > 0.f ? ff_rsqrt(d) : ffv{0.f, 0.f};
+  }
+  __syncthreads();
   for (int q = tid; q < CQ_T * CQ_T; q += CQ_THREADS) {
     const int i = q % CQ_T, j = q / CQ_T;
-    if (i < pb && j < pb && i <= j) cff_st(G, (int64_t)(p + j) * nc + p + i, sB[i][j]);
+    if (i < pb && j < pb && i <= j) {
+      const cff v = sB[i][j];
+      const cff r = i == j ? cff{ff_mul(v.re, sInv[i]), {0.f, 0.f}} : cff_scale(v, sInv[i]);
+      cff_st(G, (int64_t)(p + j) * nc + p + i, r);
+    }
   }
 }
 
@@ -416,8 +434,8 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_trsm(double *__restrict__ G, 
 // The trailing matrix: G^_ij -= sum_{k in the panel} conj(r_ki) r_kj for
 // pe <= i <= j < nc, by 32 x 32 tiles (ib <= jb over the trailing range), 256
 // threads of 2 x 2 entries, the panel's rows of both tiles' columns staged
-// in shared memory.  part 0: every tile; 1: the tiles of the next panel's
-// rows (ib = 0, one CTA per jb); 2: the others (ib >= 1).
+// in shared memory.  part 0: every tile; 2: the tiles below the next
+// panel's rows (ib >= 1), whose own update is k_cq_herk_rows.
 __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, int32_t nc, int32_t p,
                                                         int32_t part, const int32_t *__restrict__ status) {
   __shared__ cff sI[CQ_T][CQ_T];  // [panel row][column of the i tile]
@@ -425,15 +443,10 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, 
   if (*status != GN_OK) return;
   const int pb = min(CQ_T, nc - p), pe = p + pb;
   int ib, jb;
-  if (part == 1) {  // the next panel's rows only
-    ib = 0;
-    jb = blockIdx.x;
-  } else {
-    cq_tile(blockIdx.x, ib, jb);
-    if (part == 2) {  // every tile below them
-      ib++;
-      jb++;
-    }
+  cq_tile(blockIdx.x, ib, jb);
+  if (part == 2) {  // every tile below the next panel's rows
+    ib++;
+    jb++;
   }
   const int i0 = pe + ib * CQ_T, j0 = pe + jb * CQ_T;
   const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
@@ -474,6 +487,47 @@ __global__ void __launch_bounds__(CQ_THREADS) k_cq_herk(double *__restrict__ G, 
     }
 }
 
+// The trailing update of the next panel's rows alone, the step of the
+// lookahead that the next panel waits for: the same sums as k_cq_herk for
+// the tiles (0, jb), by 16 x 16 quarters of them, one entry per thread with
+// two accumulation chains, so these few tiles spread over four times the
+// CTAs and a thread's chain is half as long.
+constexpr int CQ_H = 16;
+__global__ void __launch_bounds__(CQ_H * CQ_H) k_cq_herk_rows(double *__restrict__ G, int32_t nc, int32_t p,
+                                                             const int32_t *__restrict__ status) {
+  __shared__ cff sI[CQ_T][CQ_H];  // [panel row][row of the quarter]
+  __shared__ cff sJ[CQ_T][CQ_H];  // [panel row][column of the quarter]
+  if (*status != GN_OK) return;
+  const int pb = min(CQ_T, nc - p), pe = p + pb;
+  const int jb = blockIdx.x >> 2, qd = blockIdx.x & 3;
+  const int i0 = pe + (qd >> 1) * CQ_H, j0 = pe + jb * CQ_T + (qd & 1) * CQ_H;
+  if (i0 > j0 + CQ_H - 1) return;  // a quarter below the diagonal: the whole CTA, before any barrier
+  const int tid = threadIdx.x, ty = tid / CQ_H, tx = tid % CQ_H;
+  for (int q = tid; q < CQ_T * CQ_H; q += CQ_H * CQ_H) {
+    const int k = q % CQ_T, c = q / CQ_T;
+    cff u = {{0.f, 0.f}, {0.f, 0.f}}, v = u;
+    if (k < pb) {
+      if (i0 + c < nc) u = cff_ld(G, (int64_t)(i0 + c) * nc + p + k);
+      if (j0 + c < nc) v = cff_ld(G, (int64_t)(j0 + c) * nc + p + k);
+    }
+    sI[k][c] = u;
+    sJ[k][c] = v;
+  }
+  __syncthreads();
+  cff acc[2] = {{{0.f, 0.f}, {0.f, 0.f}}, {{0.f, 0.f}, {0.f, 0.f}}};
+#pragma unroll
+  for (int k = 0; k < CQ_T; k++)
+    if (k < pb) cff_sub_conj_mul(acc[k & 1], sI[k][ty], sJ[k][tx]);
+  const int i = i0 + ty, j = j0 + tx;
+  if (i < nc && j < nc && i <= j) {
+    const int64_t at = (int64_t)j * nc + i;
+    cff g = cff_ld(G, at);
+    g.re = ff_add(g.re, ff_add(acc[0].re, acc[1].re));  // acc holds minus the sum
+    g.im = ff_add(g.im, ff_add(acc[0].im, acc[1].im));
+    cff_st(G, at, g);
+  }
+}
+
 // ---- triangular solves with the float-float factor ----
 //
 // With R^ final, the Gauss-Newton step (R dx = y) and each refinement step
@@ -498,16 +552,6 @@ constexpr int CQC_OWN = CQC_MAXN / (CQB * CQC);   // blocks per CTA
 constexpr size_t CQC_SMEM =
     sizeof(cff) * (CQC_OWN * CQB * CQB + 2 * CQC_OWN * CQB + 2 * CQB) + sizeof(double) * (CQC_THREADS / 32);
 
-// 1 / d for d > 0: the FP32 reciprocal and two Newton steps y += y (1 - d y)
-__device__ __forceinline__ ffv ff_recip(ffv d) {
-  ffv y = {__frcp_rn(d.h), 0.f};
-#pragma unroll
-  for (int it = 0; it < 2; it++) {
-    const ffv e = ff_add({1.f, 0.f}, ff_neg(ff_mul(d, y)));
-    y = ff_add(y, ff_mul(y, e));
-  }
-  return y;
-}
 
 // acc += a x, or conj(a) x
 template <bool CONJ>
@@ -888,7 +932,7 @@ gn_status launch_cholqr(int32_t N, int32_t n, const double *A, double *R, double
     if (cudaEventRecord(ev_panel, ps) != cudaSuccess) return GN_ECUDA;  // the row block is done
     // the next panel's rows: after the previous rest, which updated them too
     if (trail && cudaStreamWaitEvent(ps, ev_trail, 0) != cudaSuccess) return GN_ECUDA;
-    k_cq_herk<<<(unsigned)tb, CQ_THREADS, 0, ps>>>(R, nc, p, 1, status);
+    k_cq_herk_rows<<<(unsigned)(4 * tb), CQ_H * CQ_H, 0, ps>>>(R, nc, p, status);
     trail = tb > 1;
     if (trail) {
       if (cudaStreamWaitEvent(st, ev_panel, 0) != cudaSuccess) return GN_ECUDA;

@@ -35,6 +35,8 @@ static gn_status upload(T **p, const T *h, size_t count) {
 
 static void ws_free(Workspace &w) {
   if (w.step_exec) cudaGraphExecDestroy(w.step_exec);
+  if (w.cq_exec) cudaGraphExecDestroy(w.cq_exec);
+  if (w.ref_exec) cudaGraphExecDestroy(w.ref_exec);
   cudaFree(w.pow);
   cudaFree(w.stage_val);
   cudaFree(w.stage_d);
@@ -274,12 +276,22 @@ gn_status gn_system_set_arith(gn_system *s, gn_arith arith) {
   if (s->arith == (int32_t)arith) return GN_OK;
   s->arith = arith;
   for (Workspace &w : s->ws) w.fact = 0;
-  for (Workspace &w : s->ws)
+  for (Workspace &w : s->ws) {
     if (w.step_exec) {
       cudaGraphExecDestroy(w.step_exec);
       w.step_exec = nullptr;
       w.graph_x = nullptr;
     }
+    if (w.cq_exec) {
+      cudaGraphExecDestroy(w.cq_exec);
+      w.cq_exec = nullptr;
+    }
+    if (w.ref_exec) {
+      cudaGraphExecDestroy(w.ref_exec);
+      w.ref_exec = nullptr;
+      w.ref_x = nullptr;
+    }
+  }
   return GN_OK;
 }
 

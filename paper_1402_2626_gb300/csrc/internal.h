@@ -51,6 +51,9 @@ struct Workspace {
   // CUDA graph of one Newton step for a given x pointer and stream
   cudaGraphExec_t step_exec = nullptr;
   const double *graph_x = nullptr;
+  cudaGraphExec_t cq_exec = nullptr;   // the mixed solver's CholeskyQR double step (L = 1)
+  cudaGraphExec_t ref_exec = nullptr;  // the mixed solver's refinement step, for x at ref_x
+  const double *ref_x = nullptr;
   cudaStream_t graph_stream = nullptr;
 };
 

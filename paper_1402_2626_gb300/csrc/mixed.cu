@@ -222,6 +222,32 @@ static gn_status refine_step_cq(gn_system *s, Workspace *w1, Workspace *wL, doub
 // d_steps Gauss-Newton steps in double on w1->xmix with CholeskyQR
 // factorisations: evaluation into [J, -f], the factor R of [J, -f] (its last
 // column is y), R dx = y, x += dx; the factors of the last step stay in w1.
+// A CUDA graph of the work fn(stream) enqueues (its launches, and any side
+// stream it forks from that stream and joins back), instantiated into *exec;
+// on failure *exec stays null and the caller launches directly.
+template <class F>
+static void capture_graph(cudaGraphExec_t *exec, F &&fn) {
+  *exec = nullptr;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  cudaGraph_t g = nullptr;
+  bool ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  if (ok) {
+    ok = fn(cap) == GN_OK;
+    ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && ok;
+  }
+  if (ok && cudaGraphInstantiate(exec, g, 0) != cudaSuccess) {
+    ok = false;
+    *exec = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+  if (!ok) cudaGetLastError();
+}
+
 static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_report *r1,
                               cudaStream_t st) {
   const int32_t N = s->N, n = s->n;
@@ -260,13 +286,21 @@ static gn_status cholqr_steps(gn_system *s, Workspace *w1, int32_t d_steps, gn_r
       cudaGetLastError();
     }
   }
-  for (int32_t k = 0; k < d_steps; k++) {
-    gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, st);
+  // one double step; captured once as a graph (its pointers are the
+  // workspace's), so the host does not pace the chain of panel launches
+  auto step = [&](cudaStream_t cs) {
+    gn_status e = launch_eval_sel(s, 1, w1->xmix, w1->Ab + (int64_t)n * N * 2, 1, w1->Ab, N, cs);
     if (!e)
-      e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->cq_scratch, w1->status, st, w1->cq_side,
+      e = launch_cholqr(N, n, w1->Ab, w1->R, w1->rinv, w1->cq_scratch, w1->status, cs, w1->cq_side,
                         w1->cq_ev[0], w1->cq_ev[1]);
-    if (!e) e = launch_cq_solve(false, n, w1->R, w1->rinv + 2 * (size_t)(n + 1), nullptr, w1->dx, w1->status, st);
-    if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, st);
+    if (!e) e = launch_cq_solve(false, n, w1->R, w1->rinv + 2 * (size_t)(n + 1), nullptr, w1->dx, w1->status, cs);
+    if (!e) e = launch_update(1, n, w1->xmix, w1->dx, fnorm, w1->norms, w1->status, cs);
+    return e;
+  };
+  if (!w1->cq_exec) capture_graph(&w1->cq_exec, step);
+  for (int32_t k = 0; k < d_steps; k++) {
+    const gn_status e = w1->cq_exec ? (cudaGraphLaunch(w1->cq_exec, st) == cudaSuccess ? GN_OK : GN_ECUDA)
+                                    : step(st);
     if (e) return e;
   }
   if (cudaMemcpyAsync(w1->h_status, w1->status, sizeof(int32_t) * 2, cudaMemcpyDeviceToHost, st) !=
@@ -342,9 +376,18 @@ extern "C" gn_status gn_newton_mixed(gn_system *s, gn_prec prec, double *d_x, in
       cudaMemsetAsync(wL->norms, 0, sizeof(double) * 3 * GN_REPORT_MAX, st) != cudaSuccess)
     return GN_ECUDA;
   bool converged = false;
+  // the refinement step with CholeskyQR factors, captured once per x as a graph
+  auto rstep = [&](cudaStream_t cs) {
+    return L == 2 ? refine_step_cq<2>(s, w1, wL, d_x, cs) : refine_step_cq<4>(s, w1, wL, d_x, cs);
+  };
+  if (cq && refine_steps > 0 && (!wL->ref_exec || wL->ref_x != d_x)) {
+    if (wL->ref_exec) cudaGraphExecDestroy(wL->ref_exec);
+    capture_graph(&wL->ref_exec, rstep);
+    wL->ref_x = wL->ref_exec ? d_x : nullptr;
+  }
   for (int32_t k = 0; k < refine_steps; k++) {
     if (cq)
-      e = L == 2 ? refine_step_cq<2>(s, w1, wL, d_x, st) : refine_step_cq<4>(s, w1, wL, d_x, st);
+      e = wL->ref_exec ? (cudaGraphLaunch(wL->ref_exec, st) == cudaSuccess ? GN_OK : GN_ECUDA) : rstep(st);
     else
       e = L == 2 ? refine_step<2>(s, w1, wL, d_x, int_fact, st) : refine_step<4>(s, w1, wL, d_x, int_fact, st);
     if (e) return e;
