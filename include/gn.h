@@ -206,8 +206,12 @@ gn_status gn_newton(gn_system *s, gn_prec prec, double *d_x, int32_t steps, doub
  * system allocates the tensor-core form's scratch, kept until
  * gn_system_destroy: 32 Np nq + 2^22 nb (nb + 1) bytes (Np = N rounded up to
  * 64, nb = ceil((n+1)/128), nq = 128 nb; 434 MB at N = 1536, n = 1024); if
- * it cannot be allocated the integer-pipe form runs instead.  Otherwise the
- * double phase is MGS.
+ * it cannot be allocated the integer-pipe form runs instead.  With
+ * CholeskyQR the double step and the refinement step are each captured once
+ * as a CUDA graph and then replayed (kept with the system; the refinement's
+ * is captured again for another d_x), and the Cholesky's panels run one
+ * ahead on a second, high-priority stream that the system owns.  Otherwise
+ * the double phase is MGS.
  * Phase 2 gains about -log10(kappa(J) u_double) digits per step, so for a
  * consistent system (f(x*) = 0) it reaches the root at precision prec:
  * quad double from a double start takes three or four steps for
