@@ -180,6 +180,11 @@ __global__ void __launch_bounds__(BSB * BSB) k_bs_inv(const double *__restrict__
 // products is split over the cluster's SMs.  Every CTA runs every barrier
 // (no early exit after the first one).
 constexpr int BSC = 8;
+// rows of the blocks one CTA of the cluster owns, at most (block b in CTA b mod BSC)
+__host__ __device__ constexpr int bsc_own_rows(int n) {
+  return ((n + BSB - 1) / BSB + BSC - 1) / BSC * BSB;
+}
+static_assert(BSC < BSB, "a lane of each row's group per CTA, and one more");
 
 template <int L>
 __global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
@@ -189,7 +194,8 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
   extern __shared__ __align__(16) unsigned char bsm[];
   fx<KY> *sY = (fx<KY> *)bsm;              // [n][2], the rows of this CTA's blocks
   fx<K> *sXc = (fx<K> *)(sY + 2 * n);      // [2][BSB][2] x of the current / next block
-  int *sTc = (int *)(sXc + 2 * BSB * 2);   // [2][BSB]
+  cf<K> *sXo = (cf<K> *)(sXc + 2 * BSB * 2);  // x of this CTA's blocks, for dx at the end
+  int *sTc = (int *)(sXo + bsc_own_rows(n));  // [2][BSB]
   int *sFail = sTc + 2 * BSB;
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
@@ -220,22 +226,15 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
         const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
         p = cf_mul<K>(xk, yc);
       }
-      const cf<K> sx = cf_group16_sum<K>(p, has);
-      if (c == 0 && r < bs) {
-        for (int q = 0; q < BSC; q++) {
-          fx<K> *rx = cl.map_shared_rank(sXc, q) + 2 * (buf * BSB + r);
+      const cf<K> sx = cf_group16_sum<K>(p, has);  // in every lane of the row's group
+      if (r < bs) {
+        if (c < BSC) {  // lane c sends x_r to CTA c
+          fx<K> *rx = cl.map_shared_rank(sXc, c) + 2 * (buf * BSB + r);
           rx[0] = sx.re;
           rx[1] = sx.im;
-          cl.map_shared_rank(sTc, q)[buf * BSB + r] = sx.e;
-        }
-        double cr[L], ci[L];
-        const bool z = sx.e == CF_EZERO;
-        fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
-        fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          dx[(int64_t)(b0 + r) * W + q] = cr[q];
-          dx[(int64_t)(b0 + r) * W + L + q] = ci[q];
+          cl.map_shared_rank(sTc, c)[buf * BSB + r] = sx.e;
+        } else if (c == BSC) {
+          sXo[(k / BSC) * BSB + r] = sx;
         }
       }
     }
@@ -292,6 +291,22 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_backsub_cl(
     }
     cl.sync();
   }
+  // the owned rows' unknowns to L-limb cascades, off the steps' chain
+  if (run)
+    for (int t = tid; t < bsc_own_rows(n); t += BSB_THREADS) {
+      const int b = rank + BSC * (t / BSB), r = t % BSB;
+      if (b >= nb || r >= bsz(b)) continue;
+      const cf<K> sx = sXo[t];
+      double cr[L], ci[L];
+      const bool z = sx.e == CF_EZERO;
+      fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
+      fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        dx[(int64_t)(b * BSB + r) * W + q] = cr[q];
+        dx[(int64_t)(b * BSB + r) * W + L + q] = ci[q];
+      }
+    }
   if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
 }
 
@@ -311,7 +326,8 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_fwdsub_cl(
   extern __shared__ __align__(16) unsigned char bsm[];
   fx<KY> *sY = (fx<KY> *)bsm;              // [n][2], the rows of this CTA's blocks
   fx<K> *sXc = (fx<K> *)(sY + 2 * n);      // [2][BSB][2] w of the current / next block
-  int *sTc = (int *)(sXc + 2 * BSB * 2);   // [2][BSB]
+  cf<K> *sXo = (cf<K> *)(sXc + 2 * BSB * 2);  // w of this CTA's blocks, for the output at the end
+  int *sTc = (int *)(sXo + bsc_own_rows(n));  // [2][BSB]
   int *sFail = sTc + 2 * BSB;
   int *sE = sFail + 1;
   cg::cluster_group cl = cg::this_cluster();
@@ -365,22 +381,15 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_fwdsub_cl(
         const cf<K> yc = cf_from_fixed<K, KY>(sY[2 * (b0 + c)], sY[2 * (b0 + c) + 1], sig);
         p = cf_mul<K>(xk, yc);
       }
-      const cf<K> sx = cf_group16_sum<K>(p, has);
-      if (c == 0 && r < bs) {
-        for (int q = 0; q < BSC; q++) {
-          fx<K> *rx = cl.map_shared_rank(sXc, q) + 2 * (buf * BSB + r);
+      const cf<K> sx = cf_group16_sum<K>(p, has);  // in every lane of the row's group
+      if (r < bs) {
+        if (c < BSC) {  // lane c sends w_r to CTA c
+          fx<K> *rx = cl.map_shared_rank(sXc, c) + 2 * (buf * BSB + r);
           rx[0] = sx.re;
           rx[1] = sx.im;
-          cl.map_shared_rank(sTc, q)[buf * BSB + r] = sx.e;
-        }
-        double cr[L], ci[L];
-        const bool z = sx.e == CF_EZERO;
-        fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
-        fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
-#pragma unroll
-        for (int q = 0; q < L; q++) {
-          w[(int64_t)(b0 + r) * W + q] = cr[q];
-          w[(int64_t)(b0 + r) * W + L + q] = ci[q];
+          cl.map_shared_rank(sTc, c)[buf * BSB + r] = sx.e;
+        } else if (c == BSC) {
+          sXo[(k / BSC) * BSB + r] = sx;
         }
       }
     }
@@ -439,13 +448,29 @@ __global__ void __launch_bounds__(BSB_THREADS, 1) k_fwdsub_cl(
     }
     cl.sync();
   }
+  // the owned rows' unknowns to L-limb cascades, off the steps' chain
+  if (run)
+    for (int t = tid; t < bsc_own_rows(n); t += BSB_THREADS) {
+      const int b = rank + BSC * (t / BSB), r = t % BSB;
+      if (b >= nb || r >= bsz(b)) continue;
+      const cf<K> sx = sXo[t];
+      double cr[L], ci[L];
+      const bool z = sx.e == CF_EZERO;
+      fx_to_cascade<K, L>(sx.re, z ? 0 : -sx.e, cr);
+      fx_to_cascade<K, L>(sx.im, z ? 0 : -sx.e, ci);
+#pragma unroll
+      for (int q = 0; q < L; q++) {
+        w[(int64_t)(b * BSB + r) * W + q] = cr[q];
+        w[(int64_t)(b * BSB + r) * W + L + q] = ci[q];
+      }
+    }
   if (*sFail && tid == 0) atomicCAS(status, GN_OK, GN_ENONFINITE);
 }
 
 template <int L>
 __host__ __device__ constexpr size_t bsc_smem_bytes(int n) {
   return sizeof(fx<L + 2>) * 2 * (size_t)(n > 0 ? n : 1) + sizeof(fx<L>) * 2 * 2 * BSB +
-         sizeof(int) * (2 * BSB + 4);
+         sizeof(cf<L>) * (size_t)bsc_own_rows(n) + sizeof(int) * (2 * BSB + 4);
 }
 
 }  // namespace gn
