@@ -18,6 +18,9 @@ CASES = [
     ("square", dict(N=24, n=24, M=(8, 24), k=(1, 5), dmax=3, seed=602)),
     # above 2048 rows: CholeskyQR with the Gram matrix on the integer pipe
     ("tall", dict(N=2100, n=32, M=(3, 6), k=(1, 4), dmax=3, seed=603)),
+    # three Cholesky panels (the lookahead) and three solve blocks, the last
+    # one ragged (77 = 2 x 32 + 13)
+    ("ragged", dict(N=120, n=77, M=(4, 10), k=(1, 5), dmax=3, seed=604)),
 ]
 
 
