@@ -853,17 +853,23 @@ __global__ void __launch_bounds__(CQC_THREADS, 1) k_cq_solve(const double *__res
 gn_status launch_cq_solve(bool refine, int32_t n, const double *R, const double *sexp, const double *c,
                           double *dx, int32_t *status, cudaStream_t st) {
   if (n < 1 || n > CQC_MAXN) return GN_EINVAL;
+  // the kernels' shared-memory limit, raised once per device
+  constexpr int kDevices = 64;
   static std::mutex mu;
-  static int ready = -1;
+  static signed char ready[kDevices] = {};  // 0 not yet, 1 done, -1 refused
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return GN_ECUDA;
   {
     std::lock_guard<std::mutex> g(mu);
-    if (ready < 0)
-      ready = cudaFuncSetAttribute(k_cq_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)CQC_SMEM) == cudaSuccess &&
-              cudaFuncSetAttribute(k_cq_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)CQC_SMEM) == cudaSuccess;
+    if (ready[dev] == 0)
+      ready[dev] = cudaFuncSetAttribute(k_cq_solve<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)CQC_SMEM) == cudaSuccess &&
+                           cudaFuncSetAttribute(k_cq_solve<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                (int)CQC_SMEM) == cudaSuccess
+                       ? 1
+                       : -1;
   }
-  if (!ready) return GN_ECUDA;
+  if (ready[dev] != 1) return GN_ECUDA;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CQC);
   cfg.blockDim = dim3(CQC_THREADS);
