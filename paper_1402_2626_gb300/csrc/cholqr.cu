@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(CQ_H * CQ_H) k_cq_herk_rows(double *__restrict
 // With R^ final, the Gauss-Newton step (R dx = y) and each refinement step
 // (R^H w = c, then R dx = w) are triangular solves needed to double accuracy
 // only: the refinement's corrections carry their own residual.  R = R^ D, so
-// R dx = y is R^ z = y^ with z = D dx, and R^H w = c is R^H w = D^-1 c.
+// R dx = y is R^ z = y^ with z = D dx, and R^H w = c is (R^)^H w = D^-1 c.
 // Blocked substitution on one cluster of CQC CTAs: R^ is cut into CQB x CQB
 // diagonal blocks D_k whose inverses X_k = D_k^-1 are formed once per
 // factorisation (k_cq_binv); block b of the unknowns lives in CTA b mod CQC.
@@ -631,7 +631,10 @@ __global__ void __launch_bounds__(CQC_THREADS, 1) k_cq_solve(const double *__res
   double *smax = (double *)(sX + 2 * CQB);
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  const bool run = *status == GN_OK;  // the same in every CTA: nothing writes it before the end
+  // every CTA takes the same cluster barriers, whatever it reads here (only
+  // the non-finite check below writes the status word before the end, and
+  // then no CTA does any work)
+  const bool run = *status == GN_OK;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb = (n + CQB - 1) / CQB;
   auto bsz = [&](int b) { return min(CQB, n - b * CQB); };
