@@ -141,6 +141,38 @@ __device__ __forceinline__ cf<K> cf_pair_swap(const cf<K> &a) {
 // lane 1 the odd s, each taking the factor it lacks from the other lane by
 // one shuffle.  The dependent chain per term is the common factor plus k - 1
 // products plus k / 2, against the common factor plus 3k - 3 on one lane.
+// The terms' values alone, for an evaluation of f without J (the
+// refinement steps of the mixed solver): the common factor and then the
+// forward chain of k_monomials_cf, the same products in the same order (so
+// the same bits), and none of the partial derivatives.  Supports longer than
+// KMAXI are left to k_monomials_long_cf, as there.
+template <int L>
+__global__ void __launch_bounds__(256) k_monomial_values_cf(
+    const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
+    const double *__restrict__ coef, int64_t T, const double *__restrict__ pow, int32_t n,
+    double *__restrict__ stage_val, const int32_t *__restrict__ status) {
+  constexpr int WS = CfStore<L>::WORDS;
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= T || *status != GN_OK) return;
+  const int o0 = __ldg(mono_off + t);
+  const int k = __ldg(mono_off + t + 1) - o0;
+  if (k > KMAXI) return;  // a long support: k_monomials_long_cf
+  double cre[L], cim[L];
+#pragma unroll
+  for (int l = 0; l < L; l++) {
+    cre[l] = __ldg(coef + (int64_t)(2 * l + 0) * T + t);
+    cim[l] = __ldg(coef + (int64_t)(2 * l + 1) * T + t);
+  }
+  cf<L> a = cf_from_cascade<L, L>(cre, cim);
+  for (int s = 0; s < k; s++) {
+    uint32_t w = __ldg(occ + o0 + s);
+    int d = (int)(w & 255u);
+    if (d >= 2) a = cf_mul<L>(a, cf_ld<L>(pow + ((int64_t)(d - 2) * n + (w >> 8)) * WS));
+  }
+  for (int s = 0; s < k; s++) a = cf_mul<L>(a, cf_ld<L>(pow + (int64_t)(__ldg(occ + o0 + s) >> 8) * WS));
+  cf_st<L>(stage_val + t * WS, a);
+}
+
 template <int L, int KM>
 __global__ void __launch_bounds__(256) k_monomials2_cf(
     const int32_t *__restrict__ mono_off, const uint32_t *__restrict__ occ,
@@ -485,7 +517,10 @@ static gn_status eval_int_raw(const EvalArgs &a, cudaStream_t st) {
     // against 0.173 ms); batches time both
     const int lanes = a.lanes == 1 || a.lanes == 2 ? a.lanes : (a.kmax <= 16 ? 1 : 2);
     const unsigned nb = (unsigned)((lanes * a.T + bt - 1) / bt);
-    if (lanes == 1) {
+    if (!a.J) {  // f alone: the values, no partials
+      k_monomial_values_cf<L><<<(unsigned)((a.T + bt - 1) / bt), bt, 0, st>>>(
+          a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar, a.stage_val, a.status);
+    } else if (lanes == 1) {
       if (a.kmax <= 16)
         k_monomials_cf<L, 16><<<nb, bt, 0, st>>>(a.mono_off, a.occ, a.coef, a.T, a.pow, (int32_t)a.nvar,
                                                  a.stage_val, a.stage_d, a.status);

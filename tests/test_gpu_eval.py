@@ -140,3 +140,32 @@ def test_root_residual_dd(arith):
     f, _ = gpu_eval(s, s.point("xstar", 2), 2, "dd", arith)
     Sf, _ = term_scales(s, s.point("xstar", 2))
     assert np.all(limb_diff(f, np.zeros_like(f)) <= 1e-28 * Sf)
+
+
+@pytest.mark.parametrize("arith", ARITHS)
+@pytest.mark.parametrize("prec,L", PRECS)
+def test_f_alone_equals_f_with_j(prec, L, arith):
+    """An evaluation of f without J (the mixed solver's refinement steps)
+    forms each term's value alone; it must give the same f, bit for bit, as
+    the evaluation that also forms J, with supports short (one lane per
+    term), longer than 16 and longer than 64 (a warp per term), and match
+    the oracle."""
+    gn = _gn()
+    for seed, (N, n, M, k, dmax) in enumerate([(37, 29, (20, 45), (1, 14), 5), (48, 40, (3, 8), (17, 40), 4),
+                                               (72, 72, 2, (60, 70), 3)]):
+        system = inputs.random_system(N, n, M, k, dmax, seed=300 + seed)
+        x = system.point("x0", L)
+        s = gn.System(system, arith=arith)
+        xd = torch.tensor(np.ascontiguousarray(x[..., :L]), device="cuda")
+        f0 = torch.full((N, 2, L), np.nan, dtype=torch.float64, device="cuda")
+        f1 = torch.full((N, 2, L), np.nan, dtype=torch.float64, device="cuda")
+        J = torch.full((n, N, 2, L), np.nan, dtype=torch.float64, device="cuda")
+        s.eval(prec, xd, f0, J)
+        s.eval(prec, xd, f1, None)
+        torch.cuda.synchronize()
+        a, b = f0.cpu().numpy(), f1.cpu().numpy()
+        assert np.array_equal(a, b), (seed, float(np.nanmax(np.abs(a - b))))
+        fo, _, _ = oracle.evaluate(system, x, L, "reverse", jacobian=False, nthreads=8)
+        Sf, _ = term_scales(system, x)
+        assert np.all(limb_diff(b, fo) <= PARITY_TOL[L] * Sf)
+        s.close()
